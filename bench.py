@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the MSDA hot path on GB300.
+
+One step = one training pass of the operator over one frame of the
+outside-in 64-camera workload: msda_forward (BF16 features and weights, FP32
+accumulation and output) followed by msda_backward (atomic mode: FP32
+gradients for the features, locations and weights).  Shapes: B=1, 64 cameras,
+maps 68x120, 34x60, 17x30, 9x15 (1080p at strides 8..64), C=256, G=8,
+A=900 anchors, P=13 keypoints, 40% of (anchor, camera) pairs out of view.
+Inputs are synthetic and seeded (paper_2601_10819_gb300.inputs, workload 2).
+
+Printed: one JSON line with the metric (us/frame, lower is better), the
+Gsamples/s throughput, a roofline entry for the dominant kernel, the
+end-to-end number through the public API with host buffers, the FP64 CPU
+oracle timed on a bounded sample, and the SM clocks seen during the timed
+region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank processes its own frame (weak scaling,
+no collective on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "MSDA fwd+bwd µs/frame @64 cams bf16; Gsamples/s; % gather roofline"
+UNIT = "µs/frame"
+WORKLOAD = ("outside-in-64cam fwd+bwd: B1 Ncam64 maps 68x120/34x60/17x30/9x15 C256 G8 A900 P13, "
+            "40% of (anchor,camera) pairs out of view, BF16 feat+weights, FP32 accumulate/out/grads, "
+            "atomic backward")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample-anchors", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--deterministic", action="store_true", help="time the deterministic backward instead")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu capture, if it matches the current source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        e = d[kernel_key]
+        if e["source_sha"] != source_sha(e["sources"]):
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.lines = []
+        self.proc = None
+        try:
+            bus = torch.cuda.get_device_properties(device_index).pci_bus_id
+            sel = ["-i", f"{int(torch.cuda.get_device_properties(device_index).pci_domain_id):08X}:"
+                         f"{int(bus):02X}:{int(torch.cuda.get_device_properties(device_index).pci_device_id):02X}.0"]
+        except Exception:
+            sel = []
+        self.cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"] + sel
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, r in rows:
+            for n, flag in zip(names, r[1:]):
+                if flag.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(pr, sample_anchors):
+    """The FP64 oracle (as it stands) on the first `sample_anchors` anchors of the frame."""
+    import oracle
+    oracle.build()
+    nthreads = oracle.max_threads()
+    sub = pr.anchors(range(min(sample_anchors, pr.sampling_location.shape[1])))
+    args = [oracle._f64(t) if i in (0, 3, 4) else oracle._i32(t) for i, t in enumerate(sub.tensors())]
+    go = oracle._f64(sub.grad_out)
+    t0 = time.perf_counter()
+    oracle.forward(*args, nthreads=nthreads)
+    t1 = time.perf_counter()
+    oracle.backward(*args, go)
+    t2 = time.perf_counter()
+    A = pr.sampling_location.shape[1]
+    na = sub.sampling_location.shape[1]
+    per_frame_s = (t2 - t0) * A / na
+    return {"value": per_frame_s * 1e6, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{na} of {A} anchors of one frame (fwd on {nthreads} OpenMP threads, bwd single-threaded), "
+                      f"fwd {t1 - t0:.2f} s + bwd {t2 - t1:.2f} s, scaled by {A}/{na}"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return 0
+    from paper_2601_10819_gb300 import inputs
+    import oracle
+    oracle.build()
+    pr = inputs.make_workload(2)
+    A = pr.sampling_location.shape[1]
+    nthreads = oracle.max_threads()
+    feat = oracle._f64(pr.feat)
+    shape, start = oracle._i32(pr.spatial_shape), oracle._i32(pr.scale_start_index)
+    # size each step's anchor sample so that the whole run stays within ~2 minutes
+    budget_s = 120.0
+    per_anchor_s = 0.02
+    na = int(max(1, min(A, budget_s / max(1, args.steps + args.warmup) / per_anchor_s)))
+    times = []
+    for it in range(args.warmup + args.steps):
+        a0 = (it * na) % A
+        idx = [(a0 + j) % A for j in range(na)]
+        sub = pr.anchors(idx)
+        loc, w, go = oracle._f64(sub.sampling_location), oracle._f64(sub.weights), oracle._f64(sub.grad_out)
+        t0 = time.perf_counter()
+        oracle.forward(feat, shape, start, loc, w, nthreads=nthreads)
+        oracle.backward(feat, shape, start, loc, w, go)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt * A / na)
+    v = statistics.mean(times) * 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v / 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": f"{na} anchors of {A} per step, scaled to a frame"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    from paper_2601_10819_gb300 import build as msda_build
+    from paper_2601_10819_gb300 import inputs, msda, roofline
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        msda_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    msda.load()
+
+    pr = inputs.make_workload(2)
+    cnt = roofline.count(pr)
+    d = pr.to(dev)
+    B, sum_hw, C = d.feat.shape
+    _, A, P, K, _ = d.sampling_location.shape
+    S, G = d.weights.shape[4], d.weights.shape[5]
+    out = torch.empty(B, A, C, device=dev)
+    gf = torch.empty(B, sum_hw, C, device=dev)
+    gl = torch.empty(B, A, P, K, 2, device=dev)
+    gw = torch.empty(B, A, P, K, S, G, device=dev)
+    det = bool(args.deterministic)
+    ws = None
+    need = msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, det)
+    if need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    tensors = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+
+    def fwd():
+        msda.forward(*tensors, out=out)
+
+    def bwd():
+        msda.backward(*tensors, d.grad_out, deterministic=det, workspace=ws, grads=(gf, gl, gw))
+
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        fwd()
+        bwd()
+    torch.cuda.synchronize(dev)
+    if msda.device_status() != 0:
+        raise RuntimeError("device status set during warm-up")
+
+    # L2 read-bandwidth probe (random 512-byte rows from a 64 MB buffer, L2-resident)
+    probe_buf = torch.empty(64 << 20, dtype=torch.uint8, device=dev).random_()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, reps, rows = nsm * 4, 4, 64
+    msda.probe_read(probe_buf, reps, blocks, rows)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    msda.probe_read(probe_buf, reps, blocks, rows)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    l2_gather_gbs = blocks * 16 * reps * rows * 512 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del probe_buf
+
+    # timed region: exactly K steps, per-call events on the launching stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            fwd()
+            evs[i][1].record(stream)
+            bwd()
+            evs[i][2].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = start.elapsed_time(end)
+    fwd_ms = sum(a.elapsed_time(b) for a, b, _ in evs) / args.steps
+    bwd_ms = sum(b.elapsed_time(c) for _, b, c in evs) / args.steps
+    t = torch.tensor([total_ms, fwd_ms, bwd_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms, fwd_ms, bwd_ms = t.tolist()
+    ms_per_step = total_ms / args.steps
+    if msda.device_status() != 0:
+        raise RuntimeError("device status set during the timed region")
+
+    # end to end through the public API with host buffers (pinned), H2D + compute + D2H each step
+    h_in = [x.cpu().pin_memory() for x in (pr.feat, pr.sampling_location, pr.weights, pr.grad_out)]
+    h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in (out, gf, gl, gw)]
+    d_in = [torch.empty_like(x, device=dev) for x in h_in]
+    h2d = sum(x.numel() * x.element_size() for x in h_in)
+    d2h = sum(x.numel() * x.element_size() for x in h_out)
+
+    def e2e_step():
+        for h, dd in zip(h_in, d_in):
+            dd.copy_(h, non_blocking=True)
+        tens = (d_in[0], d.spatial_shape, d.scale_start_index, d_in[1], d_in[2])
+        msda.forward(*tens, out=out)
+        msda.backward(*tens, d_in[3], deterministic=det, workspace=ws, grads=(gf, gl, gw))
+        for h, dd in zip(h_out, (out, gf, gl, gw)):
+            h.copy_(dd, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = torch.tensor([s0.elapsed_time(s1) / args.e2e_steps], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_ms, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(e2e_ms.item())
+
+    hbm_peak, peak_src = peaks()
+    frames = world * B
+    us_per_frame = ms_per_step * 1e3 / frames
+    # dominant call and its roofline (algorithmic HBM bytes / measured duration)
+    if bwd_ms >= fwd_ms:
+        dom, dom_ms, dom_bytes = "msda_backward", bwd_ms, cnt.bwd_hbm_bytes
+        traffic = load_traffic("msda_backward_det" if det else "msda_backward_atomic")
+    else:
+        dom, dom_ms, dom_bytes = "msda_forward", fwd_ms, cnt.fwd_hbm_bytes
+        traffic = load_traffic("msda_forward")
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    t_hbm_fwd = cnt.fwd_hbm_bytes / (hbm_peak * 1e9) * 1e6
+    t_l2_fwd = cnt.fwd_l2_gather_bytes / (l2_gather_gbs * 1e9) * 1e6
+    t_hbm_bwd = cnt.bwd_hbm_bytes / (hbm_peak * 1e9) * 1e6
+    t_l2_bwd = cnt.bwd_l2_bytes / (l2_gather_gbs * 1e9) * 1e6
+    line = {
+        "metric": METRIC, "value": us_per_frame, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "accumulate": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": B, "parallelism": f"replicas x{world}",
+                   "backward": "deterministic" if det else "atomic",
+                   "l2": "inputs larger than L2 (feat 355 MB, grad_feat 710 MB per frame); no flush"},
+        "gsamples_per_s": cnt.nominal_samples * frames / (ms_per_step * 1e-3) / 1e9,
+        "inview_gsamples_per_s": cnt.inview_samples * frames / (ms_per_step * 1e-3) / 1e9,
+        "fwd_us": fwd_ms * 1e3, "bwd_us": bwd_ms * 1e3,
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes": dom_bytes},
+        "gather_roofline": {
+            "l2_gather_gbs_measured": l2_gather_gbs,
+            "fwd": {"t_hbm_us": t_hbm_fwd, "t_l2_us": t_l2_fwd, "t_roof_us": max(t_hbm_fwd, t_l2_fwd),
+                    "t_us": fwd_ms * 1e3, "frac": max(t_hbm_fwd, t_l2_fwd) / (fwd_ms * 1e3)},
+            "bwd": {"t_hbm_us": t_hbm_bwd, "t_l2_us": t_l2_bwd, "t_roof_us": max(t_hbm_bwd, t_l2_bwd),
+                    "t_us": bwd_ms * 1e3, "frac": max(t_hbm_bwd, t_l2_bwd) / (bwd_ms * 1e3)}},
+        "counts": cnt.as_dict(),
+        "e2e": {"value": e2e_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": (2 if not det else 4 + 3 * 3) * args.steps,
+        "clocks": clk.summary(),
+        "gpu": torch.cuda.get_device_name(dev),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pr, args.cpu_sample_anchors)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

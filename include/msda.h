@@ -1,0 +1,210 @@
+/*
+ * msda.h - C-ABI of the GB300 (sm_103a) Multi-Scale Deformable Aggregation
+ * library (libmsda_gb300.so).
+ *
+ * The operator (arXiv 2601.10819, Sec. 3.1, Sec. 3.2 and Sec. 5.3): every
+ * anchor's P keypoints are projected into each of Ncam cameras; each
+ * projected location is bilinearly sampled from that camera's Nscale
+ * feature maps, with zero padding outside a map; the samples are multiplied
+ * by per-group attention weights and summed into one C-channel feature per
+ * anchor.  For channel c in group g = c / (C/G):
+ *
+ *   out[b,a,c] = sum_{p,k,s} w[b,a,p,k,s,g] * S_{b,k,s}(loc[b,a,p,k])[c]
+ *
+ * S is the bilinear sample at x = u*W - 0.5, y = v*H - 0.5 of the map of
+ * camera k at scale s (pixel (i, j) is centred at ((j+0.5)/W, (i+0.5)/H));
+ * a corner outside [0,H) x [0,W) reads 0 and a point with x <= -1,
+ * x >= W, y <= -1, y >= H, or a NaN coordinate, contributes nothing.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All tensor pointers are DEVICE pointers owned by the caller, row-major
+ *   and densely packed.  The library never allocates, frees or synchronises
+ *   inside msda_forward / msda_backward / msda_forward_batched; scratch
+ *   memory is passed in by the caller.
+ * - Layouts:
+ *     feat               [B, sum_hw, C]           (feat_dtype)
+ *     spatial_shape      [Ncam, Nscale, 2] int32  (H, W) of each map
+ *     scale_start_index  [Ncam, Nscale]    int32  first row of each map
+ *                        inside one batch element's sum_hw rows; the row of
+ *                        pixel (i, j) is b*sum_hw + start[k,s] + i*W + j
+ *     sampling_location  [B, A, P, Ncam, 2] float32, normalised (u, v)
+ *     weights            [B, A, P, Ncam, Nscale, G] (weights_dtype)
+ *     out                [B, A, C]              (out_dtype), overwritten
+ * - Arithmetic: features and weights are widened to FP32 and every product
+ *   and sum is FP32; a BF16/FP16 output is rounded once, to nearest even.
+ * - Alignment: every tensor pointer must be 16-byte aligned, and
+ *   (C/G) * sizeof(feat element) must be a multiple of 16 bytes.
+ * - Every map must satisfy H >= 1, W >= 1 and start + H*W <= sum_hw.  The
+ *   shape tables live on the device, so they are checked by the kernels: a
+ *   bad map is skipped (it contributes nothing) and the device status word
+ *   is set to MSDA_ERR_OUT_OF_RANGE; read it with msda_get_device_status().
+ * - Errors are returned, never printed; no entry point aborts.
+ *   msda_last_error() gives a message for the last failing call of the
+ *   calling thread.
+ * - Streams: `stream` is a cudaStream_t (NULL = legacy default stream); all
+ *   work is enqueued on it.  The calls allocate nothing and do not
+ *   synchronise, so they may be captured in a CUDA graph, except that the
+ *   first call on a device looks up the device status word and reads
+ *   device attributes, which should happen before any capture.
+ */
+#ifndef MSDA_GB300_H
+#define MSDA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                      /* cudaStream_t == struct CUstream_st* */
+typedef struct CUstream_st* msda_stream_t;
+
+typedef enum {
+    MSDA_OK = 0,
+    MSDA_ERR_INVALID_ARG = 1,   /* null pointer, negative or inconsistent size  */
+    MSDA_ERR_UNSUPPORTED = 2,   /* alignment / channel split this build rejects */
+    MSDA_ERR_CUDA = 3,          /* a CUDA call or kernel launch failed          */
+    MSDA_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up           */
+    MSDA_ERR_OUT_OF_RANGE = 5,  /* a shape-table entry points outside feat      */
+    MSDA_ERR_WORKSPACE = 6      /* workspace missing or smaller than required   */
+} msda_status;
+
+typedef enum { MSDA_F32 = 0, MSDA_BF16 = 1, MSDA_F16 = 2 } msda_dtype;
+
+/* Launch mapping.  A NULL tuning pointer, or a zero field, picks the
+ * built-in default for that field.  For a fixed tuning every entry point
+ * except the atomic backward is bitwise reproducible run to run; two
+ * different tunings may differ in the last bits, because the warps_per_block
+ * split decides the order of the FP32 sums. */
+typedef struct {
+    int warps_per_block;   /* 1..16: warps cooperating on one anchor             */
+    int blocks_per_sm;     /* persistent batched kernel: resident blocks per SM  */
+    int reserved[6];
+} msda_tuning;
+
+/* ------------------------------------------------------------------------
+ * msda_forward - the operator above (Sec. 3.2 multi-scale multi-view
+ * feature extraction at projected keypoints; Sec. 5.3 MSDA).
+ *   feat_dtype, weights_dtype: MSDA_F32, MSDA_BF16 or MSDA_F16.
+ *   out_dtype: MSDA_F32 (default use), MSDA_BF16 or MSDA_F16.
+ *   B, sum_hw, Ncam, Nscale, A, P >= 0 (zero-size problems are no-ops,
+ *   except that out is still written when B*A > 0); C, G >= 1; C % G == 0;
+ *   Nscale <= 16.
+ * Deterministic: the same inputs give bitwise-identical outputs.
+ * ------------------------------------------------------------------------ */
+msda_status msda_forward(const void* feat, msda_dtype feat_dtype,
+                         const int32_t* spatial_shape, const int32_t* scale_start_index,
+                         const float* sampling_location,
+                         const void* weights, msda_dtype weights_dtype,
+                         void* out, msda_dtype out_dtype,
+                         int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,
+                         const msda_tuning* tuning, msda_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * msda_backward - gradients of msda_forward for the upstream gradient
+ * grad_out [B, A, C] (float32):
+ *   grad_feat    [B, sum_hw, C]             float32, overwritten
+ *   grad_loc     [B, A, P, Ncam, 2]          float32, overwritten
+ *   grad_weights [B, A, P, Ncam, Nscale, G]  float32, overwritten
+ * For each in-bound corner with bilinear weight omega:
+ *   grad_feat[row, c] += w_g * omega * grad_out[c];
+ *   grad_weights = sum over the group's channels of grad_out * S;
+ *   grad_loc = (W * dS/dx, H * dS/dy) contracted with w_g * grad_out and
+ *   summed over scales, using the bilinear patch selected by floor() at a
+ *   grid line.
+ * The paper's operator is forward-only (an inference plugin, Sec. 5.3);
+ * this is its exact adjoint, for training.
+ *
+ *   deterministic = 0: the feature gradient is scattered with FP32 vector
+ *     atomics (summation order varies run to run, values agree to rounding).
+ *   deterministic = 1: contributions are sorted by feature row with a stable
+ *     radix sort and each row is reduced in a fixed order (bitwise
+ *     reproducible).
+ * grad_loc and grad_weights are computed without atomics in both modes.
+ * workspace: device memory of at least msda_backward_workspace_size(...)
+ * bytes, 256-byte aligned (may be NULL when that size is 0).
+ * ------------------------------------------------------------------------ */
+size_t msda_backward_workspace_size(int B, int sum_hw, int C, int Ncam, int Nscale,
+                                    int A, int P, int G, int deterministic);
+
+msda_status msda_backward(const void* feat, msda_dtype feat_dtype,
+                          const int32_t* spatial_shape, const int32_t* scale_start_index,
+                          const float* sampling_location,
+                          const void* weights, msda_dtype weights_dtype,
+                          const float* grad_out,
+                          float* grad_feat, float* grad_loc, float* grad_weights,
+                          int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,
+                          int deterministic, void* workspace, size_t workspace_bytes,
+                          const msda_tuning* tuning, msda_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched serving: many independent scenes (B = 1 each) with uneven camera
+ * counts, map sizes and anchor counts, in ONE persistent launch (the
+ * paper's many-camera-stream setting, Sec. 5.3 and App. C).  Scene i has
+ * its own tensors, laid out as for msda_forward with B = 1.  All scenes
+ * share C, G, P, Nscale and the dtypes.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const void* feat;                  /* [sum_hw, C]                        */
+    const int32_t* spatial_shape;      /* [Ncam, Nscale, 2] (device)         */
+    const int32_t* scale_start_index;  /* [Ncam, Nscale]    (device)         */
+    const float* sampling_location;    /* [A, P, Ncam, 2]                    */
+    const void* weights;               /* [A, P, Ncam, Nscale, G]            */
+    void* out;                         /* [A, C], overwritten                */
+    int32_t sum_hw;
+    int32_t Ncam;
+    int32_t A;
+    int32_t unit_begin;                /* sum of A over the scenes before it */
+} msda_scene;
+
+/* Scratch needed by msda_forward_batched for num_scenes scenes. */
+size_t msda_forward_batched_workspace_size(int num_scenes);
+
+/* scenes: DEVICE array of num_scenes descriptors (unit_begin filled in by
+ * the caller as the running sum of A).  total_anchors = sum of A.
+ * max_ncam >= every scene's Ncam.  scene_done_ns (optional, device,
+ * num_scenes + 1 entries): entry 0 receives the %globaltimer value when the
+ * launch starts, entry i+1 the value when scene i's last anchor finished.
+ * The workspace is re-initialised by every call (one cudaMemsetAsync), so a
+ * captured graph can be replayed. */
+msda_status msda_forward_batched(const msda_scene* scenes, int num_scenes, int total_anchors,
+                                 int max_ncam, int Nscale, int C, int P, int G,
+                                 msda_dtype feat_dtype, msda_dtype weights_dtype,
+                                 msda_dtype out_dtype,
+                                 void* workspace, size_t workspace_bytes,
+                                 uint64_t* scene_done_ns,
+                                 const msda_tuning* tuning, msda_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Status and diagnostics
+ * ------------------------------------------------------------------------ */
+/* Synchronises `stream`, returns the device status word of the current
+ * device (MSDA_OK if no kernel reported a problem since the last read) and
+ * clears it. */
+msda_status msda_get_device_status(msda_stream_t stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* msda_last_error(void);
+
+/* Library version string. */
+const char* msda_version(void);
+
+/* ------------------------------------------------------------------------
+ * Measurement aid (no counterpart in the paper): streams `bytes` bytes of
+ * `buf` (device, 16-byte aligned, bytes a multiple of 16) `reps` times with
+ * 128-bit loads, in `blocks` blocks of 512 threads, and writes one word per
+ * block to `sink` (device, >= blocks words) so the loads are not removed.
+ * A buffer smaller than L2 measures L2 read bandwidth, a larger one HBM.
+ * rows > 0 switches to random row gathers: each warp reads `rows`
+ * pseudo-random 512-byte rows of buf per rep (the access pattern of the
+ * operator's corner loads).
+ * ------------------------------------------------------------------------ */
+msda_status msda_probe_read(const void* buf, size_t bytes, int reps, int blocks, int rows,
+                            uint32_t* sink, msda_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSDA_GB300_H */

@@ -1,0 +1,226 @@
+// MSDA backward, atomic mode (sm_103a).
+//
+// Gradients of the forward of fwd.cu for the upstream gradient go[b, a, :]:
+//   dfeat[row, c] += w_g * omega * go[c]          for every in-bound corner
+//   dw[b,a,p,k,s,g] = sum_{c in g} go[c] * S[c]
+//   du = sum_s W_s * w_g * sum_c go[c] ((1-fy)(F01-F00) + fy(F11-F10))
+//   dv = sum_s H_s * w_g * sum_c go[c] ((1-fx)(F10-F00) + fx(F11-F01))
+// (the paper's operator is an inference plugin, Sec. 5.3; this is the
+// exact adjoint of the forward).
+//
+// Mapping: as in the forward, one block per anchor and one team of rt lanes
+// per (camera, keypoint) item, each lane owning CPL contiguous channels.  The
+// lane keeps its slice of go in registers for the whole anchor.  One pass
+// over the item re-reads the four corners, reduces dw over the group's lanes
+// and du/dv over the team with shuffles (fixed trees, no atomics: those two
+// gradients are bitwise reproducible), and scatters the feature gradient
+// with 16-byte FP32 vector atomics (red.global.add.v4.f32).
+#include "common.cuh"
+#include "internal.h"
+
+namespace msda {
+
+struct BwdArgs {
+    const void* feat;
+    const int32_t* shape;
+    const int32_t* start;
+    const float* loc;
+    const void* w;
+    const float* go;
+    float* gfeat;
+    float* gloc;
+    float* gw;
+    int B, sum_hw, C, Ncam, Nscale, A, P, G, Cg;
+    int rt;
+    int scatter;  // 0: skip the feature-gradient atomics (deterministic mode)
+    int* status;
+};
+
+__device__ __forceinline__ float4 scale4(float a, const float4& v) {
+    return make_float4(a * v.x, a * v.y, a * v.z, a * v.w);
+}
+
+__device__ __forceinline__ float team_sum(float v, unsigned mask, int width) {
+    for (int off = width >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
+template <typename FT, typename WT, int NV>
+__global__ void __launch_bounds__(512) bwd_atomic_kernel(const BwdArgs p) {
+    constexpr int VEC = Elem<FT>::VEC;
+    constexpr int CPL = VEC * NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nmaps = p.Ncam * p.Nscale;
+    MapInfo* smap = reinterpret_cast<MapInfo*>(smem);
+    float2* sloc = reinterpret_cast<float2*>(smem + align16(sizeof(MapInfo) * (size_t)nmaps));
+
+    const long long ba = blockIdx.x;
+    const int b = (int)(ba / p.A);
+    for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
+        smap[i] = load_map(p.shape, p.start, i, p.sum_hw, p.status);
+    const float2* gl = reinterpret_cast<const float2*>(p.loc) + ba * (long long)(p.P * p.Ncam);
+    for (int i = threadIdx.x; i < p.P * p.Ncam; i += blockDim.x) sloc[i] = __ldg(gl + i);
+    __syncthreads();
+
+    const int tpw = 32 / p.rt;
+    const int nteams = (blockDim.x >> 5) * tpw;
+    const int lane = threadIdx.x & 31;
+    const int tiw = lane / p.rt;
+    const int team = (threadIdx.x >> 5) * tpw + tiw;
+    const int tl = lane & (p.rt - 1);
+    const unsigned tmask = (p.rt == 32) ? 0xffffffffu : (((1u << p.rt) - 1u) << (tiw * p.rt));
+    const int c0 = tl * CPL;
+    const int g = c0 / p.Cg;
+    const int lg = p.Cg / CPL;  // lanes per group (power of two)
+
+    const FT* fb = reinterpret_cast<const FT*>(p.feat) + (long long)b * p.sum_hw * p.C + c0;
+    float* gfb = p.gfeat + (long long)b * p.sum_hw * p.C + c0;
+    const long long wanchor = ba * ((long long)p.P * p.Ncam * p.Nscale * p.G);
+    const WT* wb = reinterpret_cast<const WT*>(p.w) + wanchor + g;
+    float* gwb = p.gw + wanchor + g;
+
+    float go[CPL];
+    {
+        const float4* gsrc = reinterpret_cast<const float4*>(p.go + ba * p.C + c0);
+#pragma unroll
+        for (int j = 0; j < CPL / 4; ++j) {
+            const float4 t = __ldg(gsrc + j);
+            go[4 * j + 0] = t.x; go[4 * j + 1] = t.y; go[4 * j + 2] = t.z; go[4 * j + 3] = t.w;
+        }
+    }
+
+    const int nitems = p.Ncam * p.P;
+    for (int item = team; item < nitems; item += nteams) {
+        const int k = item / p.P;
+        const int pp = item - k * p.P;
+        const float2 uv = sloc[pp * p.Ncam + k];
+        const long long pk = (long long)pp * p.Ncam + k;
+        const WT* wrow = wb + pk * p.Nscale * p.G;
+        float* gwrow = gwb + pk * p.Nscale * p.G;
+        const MapInfo* mrow = smap + k * p.Nscale;
+        float du = 0.0f, dv = 0.0f;
+        for (int s = 0; s < p.Nscale; ++s) {
+            const MapInfo m = mrow[s];
+            Cell c;
+            const bool in = (m.W != 0) && locate(uv.x, uv.y, m.H, m.W, c);  // uniform over the team
+            float dwp = 0.0f;
+            if (in) {
+                const float wv = ldw(wrow + (long long)s * p.G);
+                const bool vx0 = c.x0 >= 0, vx1 = c.x0 + 1 < m.W;
+                const bool vy0 = c.y0 >= 0, vy1 = c.y0 + 1 < m.H;
+                const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
+                const float o00 = ax * ay, o01 = c.fx * ay, o10 = ax * c.fy, o11 = c.fx * c.fy;
+                const long long r00 = (long long)(m.start + c.y0 * m.W + c.x0) * p.C;
+                const long long rW = (long long)m.W * p.C;
+                const FT* p00 = fb + r00;
+                uint4 q00[NV], q01[NV], q10[NV], q11[NV];
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    q00[n] = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
+                    q01[n] = (vy0 && vx1) ? ld16(p00 + p.C + n * VEC) : z;
+                    q10[n] = (vy1 && vx0) ? ld16(p00 + rW + n * VEC) : z;
+                    q11[n] = (vy1 && vx1) ? ld16(p00 + rW + p.C + n * VEC) : z;
+                }
+                float gxp = 0.0f, gyp = 0.0f;
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    float f00[VEC], f01[VEC], f10[VEC], f11[VEC];
+                    widen(q00[n], f00, FT());
+                    widen(q01[n], f01, FT());
+                    widen(q10[n], f10, FT());
+                    widen(q11[n], f11, FT());
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        const float gj = go[n * VEC + j];
+                        const float S = o00 * f00[j] + o01 * f01[j] + o10 * f10[j] + o11 * f11[j];
+                        dwp = fmaf(gj, S, dwp);
+                        gxp = fmaf(gj, ay * (f01[j] - f00[j]) + c.fy * (f11[j] - f10[j]), gxp);
+                        gyp = fmaf(gj, ax * (f10[j] - f00[j]) + c.fx * (f11[j] - f01[j]), gyp);
+                    }
+                }
+                du = fmaf((float)m.W * wv, gxp, du);
+                dv = fmaf((float)m.H * wv, gyp, dv);
+                // feature gradient: w * omega * go for each in-bound corner
+                if (p.scatter) {
+                    float* g00 = gfb + r00;
+                    const float c00 = wv * o00, c01 = wv * o01, c10 = wv * o10, c11 = wv * o11;
+#pragma unroll
+                    for (int j = 0; j < CPL; j += 4) {
+                        const float4 gv = make_float4(go[j], go[j + 1], go[j + 2], go[j + 3]);
+                        if (vy0 && vx0) atomicAdd(reinterpret_cast<float4*>(g00 + j), scale4(c00, gv));
+                        if (vy0 && vx1) atomicAdd(reinterpret_cast<float4*>(g00 + p.C + j), scale4(c01, gv));
+                        if (vy1 && vx0) atomicAdd(reinterpret_cast<float4*>(g00 + rW + j), scale4(c10, gv));
+                        if (vy1 && vx1) atomicAdd(reinterpret_cast<float4*>(g00 + rW + p.C + j), scale4(c11, gv));
+                    }
+                }
+            }
+            // weight gradient of group g at this scale: reduce over the group's lanes
+            const float dw = team_sum(dwp, tmask, lg);
+            if ((tl & (lg - 1)) == 0) gwrow[(long long)s * p.G] = dw;
+        }
+        du = team_sum(du, tmask, p.rt);
+        dv = team_sum(dv, tmask, p.rt);
+        if (tl == 0) {
+            float2* dst = reinterpret_cast<float2*>(p.gloc) + (ba * p.P + pp) * p.Ncam + k;
+            *dst = make_float2(du, dv);
+        }
+    }
+}
+
+using BwdKernel = void (*)(const BwdArgs);
+
+template <typename FT, typename WT>
+static BwdKernel bwd_pick_nv(int nv) {
+    switch (nv) {
+        case 1: return bwd_atomic_kernel<FT, WT, 1>;
+        case 2: return bwd_atomic_kernel<FT, WT, 2>;
+        case 4: return bwd_atomic_kernel<FT, WT, 4>;
+    }
+    return nullptr;
+}
+
+static BwdKernel bwd_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
+    if (ft == MSDA_F32 && wt == MSDA_F32) return bwd_pick_nv<float, float>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_BF16) return bwd_pick_nv<__nv_bfloat16, __nv_bfloat16>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_F32) return bwd_pick_nv<__nv_bfloat16, float>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F16) return bwd_pick_nv<__half, __half>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F32) return bwd_pick_nv<__half, float>(nv);
+    return nullptr;
+}
+
+size_t bwd_smem_bytes(const Problem& p) {
+    return align16(sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale) + sizeof(float2) * (size_t)p.P * p.Ncam;
+}
+
+msda_status launch_backward_atomic(const Problem& p, const float* grad_out, float* grad_feat,
+                                   float* grad_loc, float* grad_w, int warps, cudaStream_t stream) {
+    return launch_backward_loc_w(p, grad_out, grad_feat, grad_loc, grad_w, warps, 1, stream);
+}
+
+msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float* grad_feat,
+                                  float* grad_loc, float* grad_w, int warps, int scatter,
+                                  cudaStream_t stream) {
+    DeviceInfo dev;
+    msda_status st = device_info(&dev);
+    if (st != MSDA_OK) return st;
+    BwdKernel k = bwd_kernel_for(p.feat_t, p.w_t, p.nv);
+    if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: unsupported feature/weight dtype pair");
+    const size_t feat_bytes = sizeof(float) * (size_t)p.B * p.sum_hw * p.C;
+    if (scatter && feat_bytes && cudaMemsetAsync(grad_feat, 0, feat_bytes, stream) != cudaSuccess)
+        return check_launch("msda_backward memset");
+    const long long nblocks = (long long)p.B * p.A;
+    if (nblocks == 0) return MSDA_OK;
+    const size_t smem = bwd_smem_bytes(p);
+    st = ensure_smem((const void*)k, smem, dev);
+    if (st != MSDA_OK) return st;
+    BwdArgs a;
+    a.feat = p.feat; a.shape = p.shape; a.start = p.start; a.loc = p.loc; a.w = p.w;
+    a.go = grad_out; a.gfeat = grad_feat; a.gloc = grad_loc; a.gw = grad_w;
+    a.B = p.B; a.sum_hw = p.sum_hw; a.C = p.C; a.Ncam = p.Ncam; a.Nscale = p.Nscale;
+    a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.scatter = scatter; a.status = dev.status;
+    k<<<(unsigned)nblocks, warps * 32, smem, stream>>>(a);
+    return check_launch("msda_backward");
+}
+
+}  // namespace msda

@@ -1,0 +1,368 @@
+// MSDA backward, deterministic feature gradient (sm_103a).
+//
+// The feature gradient is a scatter: every in-bound corner of every sampled
+// point adds w_g * omega * go[c] to one feature row.  Scattering with
+// atomics makes the FP32 summation order depend on timing.  This mode
+// instead gathers: it builds, for every corner of every point-scale, the
+// key (feature row) and the value (the corner's slot id 4*pt + q), sorts
+// the pairs by key with a stable LSD radix sort, so that equal rows keep the
+// slot order, and then lets one team per feature row sum its contributions
+// in that order and write the row once (rows nobody touches get zeros, so
+// no memset is needed).  The result is bitwise reproducible for any launch.
+//
+// Point-scale index pt = ((((b*A + a)*P + p)*Ncam + k)*Nscale + s).  The
+// reduce kernel recomputes the corner weight omega from the location with
+// the same arithmetic as every other kernel, so keys and weights agree.
+#include "common.cuh"
+#include "internal.h"
+
+namespace msda {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kTile = kSortThreads * kSortItems;  // keys per sort block
+
+struct DetLayout {
+    size_t n;       // slots: 4 per point-scale
+    size_t nrows;   // B * sum_hw
+    int nb;         // sort tiles
+    int passes;     // 8-bit digit passes
+    size_t k0, v0, k1, v1, hist, tot, rowptr, total;
+};
+
+static DetLayout det_layout(long long npts, long long nrows) {
+    DetLayout L;
+    L.n = (size_t)npts * 4;
+    L.nrows = (size_t)nrows;
+    L.nb = (int)((L.n + kTile - 1) / kTile);
+    int bits = 0;
+    while (bits < 32 && ((unsigned long long)nrows >> bits) != 0) ++bits;  // keys go up to nrows
+    L.passes = (bits + 7) / 8;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.k0 = take(4 * L.n);
+    L.v0 = take(4 * L.n);
+    L.k1 = take(4 * L.n);
+    L.v1 = take(4 * L.n);
+    L.hist = take(4 * (size_t)256 * (L.nb > 0 ? L.nb : 1));
+    L.tot = take(4 * 256);
+    L.rowptr = take(4 * (L.nrows + 1));
+    L.total = off;
+    return L;
+}
+
+size_t backward_det_workspace(const Problem& p) {
+    const long long npts = (long long)p.B * p.A * p.P * p.Ncam * p.Nscale;
+    return det_layout(npts, (long long)p.B * p.sum_hw).total;
+}
+
+// ---------------------------------------------------------------------------
+// 1. Keys and slot ids
+// ---------------------------------------------------------------------------
+struct KeyArgs {
+    const int32_t* shape;
+    const int32_t* start;
+    const float* loc;
+    uint32_t* keys;
+    uint32_t* vals;
+    long long npts;
+    int sum_hw, A, P, Ncam, Nscale;
+    uint32_t sentinel;
+    int* status;
+};
+
+__global__ void __launch_bounds__(256) det_keys_kernel(const KeyArgs a) {
+    for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < a.npts;
+         pt += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(pt % a.Nscale);
+        const long long t = pt / a.Nscale;            // ((b*A + a)*P + p)*Ncam + k
+        const int k = (int)(t % a.Ncam);
+        const long long b = t / ((long long)a.Ncam * a.P * a.A);
+        const MapInfo m = load_map(a.shape, a.start, k * a.Nscale + s, a.sum_hw, a.status);
+        const float2 uv = __ldg(reinterpret_cast<const float2*>(a.loc) + t);
+        Cell c;
+        const bool in = (m.W != 0) && locate(uv.x, uv.y, m.H, m.W, c);
+        uint32_t key[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = c.y0 + (q >> 1), j = c.x0 + (q & 1);
+            const bool ok = in && i >= 0 && i < m.H && j >= 0 && j < m.W;
+            key[q] = ok ? (uint32_t)(b * a.sum_hw + m.start + i * m.W + j) : a.sentinel;
+        }
+        const uint32_t slot = (uint32_t)(pt * 4);
+        reinterpret_cast<uint4*>(a.keys)[pt] = make_uint4(key[0], key[1], key[2], key[3]);
+        reinterpret_cast<uint4*>(a.vals)[pt] = make_uint4(slot, slot + 1, slot + 2, slot + 3);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Stable LSD radix sort, 8-bit digits: histogram, per-digit scan, scatter
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t* __restrict__ keys, size_t n,
+                                                                  int shift, uint32_t* __restrict__ hist, int nb) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * kTile;
+#pragma unroll 4
+    for (int r = 0; r < kSortItems; ++r) {
+        const size_t i = base + (size_t)r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(__ldg(keys + i) >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// Inclusive scan of one value per thread over a block of 32*W threads.
+template <int W>
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_sums[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < W ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < W) warp_sums[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t r = v + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    if (total) *total = warp_sums[W - 1];
+    __syncthreads();
+    return r;
+}
+
+// Block d turns hist[d][0..nb) into exclusive prefixes and writes totals[d].
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ hist, int nb,
+                                                          uint32_t* __restrict__ totals) {
+    __shared__ uint32_t ws[32];
+    uint32_t* h = hist + (size_t)blockIdx.x * nb;
+    uint32_t carry = 0;
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nb ? h[i] : 0u;
+        uint32_t tot;
+        const uint32_t incl = block_inclusive_scan<32>(v, ws, &tot);
+        if (i < nb) h[i] = carry + incl - v;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ hist,
+    const uint32_t* __restrict__ totals, int nb) {
+    constexpr int NW = kSortThreads / 32;
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[NW][256];
+    __shared__ uint32_t ws[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    {
+        const uint32_t tot = totals[t];
+        const uint32_t incl = block_inclusive_scan<NW>(tot, ws, nullptr);
+        base[t] = incl - tot + hist[(size_t)t * nb + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) wcnt[w][t] = 0u;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    const size_t tile = (size_t)blockIdx.x * kTile;
+    for (int r = 0; r < kSortItems; ++r) {
+        const size_t i = tile + (size_t)r * kSortThreads + t;
+        const bool ok = i < n;
+        const uint32_t key = ok ? kin[i] : 0u;
+        const uint32_t val = ok ? vin[i] : 0u;
+        const int d = ok ? (int)((key >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (ok) {
+            uint32_t pos = base[d] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            sum += wcnt[w][t];
+            wcnt[w][t] = 0u;
+        }
+        base[t] += sum;
+        __syncthreads();
+    }
+}
+
+// rowptr[r] = number of sorted keys < r, for r in [0, nrows].
+__global__ void __launch_bounds__(256) row_ptr_kernel(const uint32_t* __restrict__ ks, size_t n,
+                                                      uint32_t nrows, uint32_t* __restrict__ rowptr) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i <= n; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long lo = (i == 0) ? 0ull : (unsigned long long)ks[i - 1] + 1ull;
+        unsigned long long hi = (i == n) ? (unsigned long long)nrows : (unsigned long long)ks[i];
+        if (hi > nrows) hi = nrows;
+        for (unsigned long long r = lo; r <= hi; ++r) rowptr[r] = (uint32_t)i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. Fixed-order segment reduce: one team of rt lanes per feature row
+// ---------------------------------------------------------------------------
+struct RedArgs {
+    const int32_t* shape;
+    const int32_t* start;
+    const float* loc;
+    const void* w;
+    const float* go;
+    const uint32_t* vals;
+    const uint32_t* rowptr;
+    float* gfeat;
+    long long nrows;
+    int sum_hw, C, Ncam, Nscale, A, P, G, Cg, rt;
+    int* status;
+};
+
+template <typename WT, int CPL>
+__global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    MapInfo* smap = reinterpret_cast<MapInfo*>(smem);
+    const int nmaps = a.Ncam * a.Nscale;
+    for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
+        smap[i] = load_map(a.shape, a.start, i, a.sum_hw, nullptr);
+    __syncthreads();
+    const int tpw = 32 / a.rt;
+    const int nteams = (blockDim.x >> 5) * tpw;
+    const int lane = threadIdx.x & 31;
+    const int team = (threadIdx.x >> 5) * tpw + lane / a.rt;
+    const int c0 = (lane & (a.rt - 1)) * CPL;
+    const int g = c0 / a.Cg;
+    const long long row = (long long)blockIdx.x * nteams + team;
+    if (row >= a.nrows) return;
+    const WT* wp = reinterpret_cast<const WT*>(a.w);
+    float acc[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) acc[j] = 0.0f;
+    const uint32_t e0 = a.rowptr[row], e1 = a.rowptr[row + 1];
+    const long long per_anchor = (long long)a.P * a.Ncam;
+    for (uint32_t e = e0; e < e1; ++e) {
+        const uint32_t slot = __ldg(a.vals + e);
+        const long long pt = slot >> 2;
+        const int q = (int)(slot & 3u);
+        const int s = (int)(pt % a.Nscale);
+        const long long t = pt / a.Nscale;
+        const int k = (int)(t % a.Ncam);
+        const long long ba = t / per_anchor;
+        const MapInfo m = smap[k * a.Nscale + s];
+        const float2 uv = __ldg(reinterpret_cast<const float2*>(a.loc) + t);
+        Cell c;
+        locate(uv.x, uv.y, m.H, m.W, c);  // in range: the key was valid
+        const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
+        const float om = (q == 0) ? ax * ay : (q == 1) ? c.fx * ay : (q == 2) ? ax * c.fy : c.fx * c.fy;
+        const float coef = ldw(wp + pt * a.G + g) * om;
+        const float4* gsrc = reinterpret_cast<const float4*>(a.go + ba * a.C + c0);
+#pragma unroll
+        for (int j = 0; j < CPL / 4; ++j) {
+            const float4 v = __ldg(gsrc + j);
+            acc[4 * j + 0] = fmaf(coef, v.x, acc[4 * j + 0]);
+            acc[4 * j + 1] = fmaf(coef, v.y, acc[4 * j + 1]);
+            acc[4 * j + 2] = fmaf(coef, v.z, acc[4 * j + 2]);
+            acc[4 * j + 3] = fmaf(coef, v.w, acc[4 * j + 3]);
+        }
+    }
+    float4* dst = reinterpret_cast<float4*>(a.gfeat + row * a.C + c0);
+#pragma unroll
+    for (int j = 0; j < CPL / 4; ++j) dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+}
+
+using RedKernel = void (*)(const RedArgs);
+
+template <typename WT>
+static RedKernel red_pick(int cpl) {
+    switch (cpl) {
+        case 4: return det_reduce_kernel<WT, 4>;
+        case 8: return det_reduce_kernel<WT, 8>;
+        case 16: return det_reduce_kernel<WT, 16>;
+        case 32: return det_reduce_kernel<WT, 32>;
+    }
+    return nullptr;
+}
+
+msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
+                                float* grad_loc, float* grad_w, void* ws, size_t ws_bytes,
+                                int warps, cudaStream_t stream) {
+    DeviceInfo dev;
+    msda_status st = device_info(&dev);
+    if (st != MSDA_OK) return st;
+    const long long npts = (long long)p.B * p.A * p.P * p.Ncam * p.Nscale;
+    const long long nrows = (long long)p.B * p.sum_hw;
+    if (npts * 4 >= (1ll << 32) || nrows >= (1ll << 32) - 1)
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: deterministic mode limited to 2^32 corner slots and rows");
+    const DetLayout L = det_layout(npts, nrows);
+    if (!ws || ws_bytes < L.total)
+        return fail(MSDA_ERR_WORKSPACE, "msda_backward: deterministic mode needs %zu workspace bytes", L.total);
+    const int cpl = p.C / p.rt;
+    RedKernel red = (p.w_t == MSDA_F32) ? red_pick<float>(cpl)
+                  : (p.w_t == MSDA_BF16) ? red_pick<__nv_bfloat16>(cpl) : red_pick<__half>(cpl);
+    if (!red) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: no reduce kernel for %d channels per lane", cpl);
+
+    // dloc and dw (no feature scatter)
+    st = launch_backward_loc_w(p, grad_out, grad_feat, grad_loc, grad_w, warps, 0, stream);
+    if (st != MSDA_OK) return st;
+    if (nrows == 0) return MSDA_OK;
+
+    unsigned char* base = reinterpret_cast<unsigned char*>(ws);
+    uint32_t* kbuf[2] = {reinterpret_cast<uint32_t*>(base + L.k0), reinterpret_cast<uint32_t*>(base + L.k1)};
+    uint32_t* vbuf[2] = {reinterpret_cast<uint32_t*>(base + L.v0), reinterpret_cast<uint32_t*>(base + L.v1)};
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + L.hist);
+    uint32_t* tot = reinterpret_cast<uint32_t*>(base + L.tot);
+    uint32_t* rowptr = reinterpret_cast<uint32_t*>(base + L.rowptr);
+    int cur = 0;
+    if (npts > 0) {
+        KeyArgs ka;
+        ka.shape = p.shape; ka.start = p.start; ka.loc = p.loc; ka.keys = kbuf[0]; ka.vals = vbuf[0];
+        ka.npts = npts; ka.sum_hw = p.sum_hw; ka.A = p.A; ka.P = p.P; ka.Ncam = p.Ncam;
+        ka.Nscale = p.Nscale; ka.sentinel = (uint32_t)nrows; ka.status = dev.status;
+        long long kb = (npts + 255) / 256;
+        if (kb > (long long)dev.sm_count * 64) kb = (long long)dev.sm_count * 64;
+        det_keys_kernel<<<(unsigned)kb, 256, 0, stream>>>(ka);
+        if ((st = check_launch("msda_backward keys")) != MSDA_OK) return st;
+        for (int pass = 0; pass < L.passes; ++pass) {
+            const int shift = 8 * pass;
+            radix_hist_kernel<<<L.nb, kSortThreads, 0, stream>>>(kbuf[cur], L.n, shift, hist, L.nb);
+            radix_scan_kernel<<<256, 1024, 0, stream>>>(hist, L.nb, tot);
+            radix_scatter_kernel<<<L.nb, kSortThreads, 0, stream>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1],
+                                                                    vbuf[cur ^ 1], L.n, shift, hist, tot, L.nb);
+            if ((st = check_launch("msda_backward sort")) != MSDA_OK) return st;
+            cur ^= 1;
+        }
+    }
+    {
+        long long rb = ((long long)L.n + 1 + 255) / 256;
+        if (rb > (long long)dev.sm_count * 32) rb = (long long)dev.sm_count * 32;
+        row_ptr_kernel<<<(unsigned)rb, 256, 0, stream>>>(kbuf[cur], L.n, (uint32_t)nrows, rowptr);
+        if ((st = check_launch("msda_backward row offsets")) != MSDA_OK) return st;
+    }
+    RedArgs ra;
+    ra.shape = p.shape; ra.start = p.start; ra.loc = p.loc; ra.w = p.w; ra.go = grad_out;
+    ra.vals = vbuf[cur]; ra.rowptr = rowptr; ra.gfeat = grad_feat; ra.nrows = nrows;
+    ra.sum_hw = p.sum_hw; ra.C = p.C; ra.Ncam = p.Ncam; ra.Nscale = p.Nscale; ra.A = p.A; ra.P = p.P;
+    ra.G = p.G; ra.Cg = p.Cg; ra.rt = p.rt; ra.status = dev.status;
+    const int nteams = 8 * (32 / p.rt);
+    const long long rblocks = (nrows + nteams - 1) / nteams;
+    const size_t smem = sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale;
+    if ((st = ensure_smem((const void*)red, smem, dev)) != MSDA_OK) return st;
+    red<<<(unsigned)rblocks, 256, smem, stream>>>(ra);
+    return check_launch("msda_backward reduce");
+}
+
+}  // namespace msda

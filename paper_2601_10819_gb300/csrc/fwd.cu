@@ -1,0 +1,383 @@
+// MSDA forward kernels (sm_103a).
+//
+// The operator (arXiv 2601.10819, Sec. 3.2 and Sec. 5.3): for every anchor,
+// keypoint p, camera k and scale s, bilinearly sample the projected
+// location from the camera's map (zero padding), weight the sample by the
+// per-group attention weight and sum everything into out[b, a, :].
+//
+// Mapping.  One block owns one anchor (b, a).  Its threads form "teams" of
+// rt lanes; a team covers the anchor's whole channel row, each lane owning
+// CPL = VEC * NV contiguous channels (VEC = 16 bytes of features), so every
+// corner read is one (NV) 16-byte load per lane and a team reads a whole
+// feature row with coalesced, sector-aligned loads.  The block's work items
+// are the (camera, keypoint) pairs in camera-major order, dealt round-robin
+// to its teams; each item covers every scale.  Because all resident blocks
+// walk the cameras in the same order, the maps being read at any moment
+// belong to a few cameras, which keeps them in L2 (the operator reads each
+// feature row about ten times).  The sampling locations of the anchor and
+// the map table are staged in shared memory first; the weights are read
+// only for points that are in view (a point whose bilinear footprint misses
+// the map costs no weight or feature traffic).
+//
+// Accumulation is FP32 in registers in a fixed order; the teams' partial
+// rows are summed in team order through shared memory, so a given launch
+// configuration is bitwise reproducible.
+#include "common.cuh"
+#include "internal.h"
+
+namespace msda {
+
+struct FwdArgs {
+    const void* feat;
+    const int32_t* shape;
+    const int32_t* start;
+    const float* loc;
+    const void* w;
+    void* out;
+    int out_t;
+    int B, sum_hw, C, Ncam, Nscale, A, P, G, Cg;
+    int rt;
+    int* status;
+};
+
+// Shared-memory carve-up of a forward block.
+struct FwdSmem {
+    size_t maps, loc, part, total;
+    __host__ __device__ FwdSmem(int nmaps, int P, int Ncam, int nteams, int C) {
+        maps = 0;
+        loc = align_up_dev(sizeof(MapInfo) * (size_t)nmaps, 16);
+        part = loc + align_up_dev(sizeof(float2) * (size_t)P * Ncam, 16);
+        total = part + sizeof(float) * (size_t)nteams * C;
+    }
+    __host__ __device__ static size_t align_up_dev(size_t x, size_t a) { return (x + a - 1) / a * a; }
+};
+
+// Accumulate the items of one anchor dealt to this team.
+//   fb: feat of batch element b, offset to the lane's first channel
+//   wb: weights of the anchor, offset to the lane's group
+template <typename FT, typename WT, int NV>
+__device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, const WT* __restrict__ wb,
+                                                  const MapInfo* __restrict__ smap,
+                                                  const float2* __restrict__ sloc, int C, int Ncam,
+                                                  int Nscale, int P, int G, int team, int nteams,
+                                                  float* acc) {
+    constexpr int VEC = Elem<FT>::VEC;
+    const int nitems = Ncam * P;
+    for (int item = team; item < nitems; item += nteams) {
+        const int k = item / P;
+        const int pp = item - k * P;
+        const float2 uv = sloc[pp * Ncam + k];
+        const WT* wrow = wb + ((long long)pp * Ncam + k) * Nscale * G;
+        const MapInfo* mrow = smap + k * Nscale;
+        for (int s0 = 0; s0 < Nscale; s0 += kScaleChunk) {
+#pragma unroll
+            for (int ds = 0; ds < kScaleChunk; ++ds) {
+                const int s = s0 + ds;
+                if (s >= Nscale) break;
+                const MapInfo m = mrow[s];
+                Cell c;
+                if (m.W == 0 || !locate(uv.x, uv.y, m.H, m.W, c)) continue;
+                const float wv = ldw(wrow + (long long)s * G);
+                const bool vx0 = c.x0 >= 0, vx1 = c.x0 + 1 < m.W;
+                const bool vy0 = c.y0 >= 0, vy1 = c.y0 + 1 < m.H;
+                const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
+                const float w00 = wv * (ax * ay), w01 = wv * (c.fx * ay);
+                const float w10 = wv * (ax * c.fy), w11 = wv * (c.fx * c.fy);
+                const long long r00 = (long long)(m.start + c.y0 * m.W + c.x0) * C;
+                const FT* p00 = fb + r00;
+                const FT* p01 = p00 + C;
+                const FT* p10 = p00 + (long long)m.W * C;
+                const FT* p11 = p10 + C;
+                uint4 q00[NV], q01[NV], q10[NV], q11[NV];
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    q00[n] = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
+                    q01[n] = (vy0 && vx1) ? ld16(p01 + n * VEC) : z;
+                    q10[n] = (vy1 && vx0) ? ld16(p10 + n * VEC) : z;
+                    q11[n] = (vy1 && vx1) ? ld16(p11 + n * VEC) : z;
+                }
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    float f00[VEC], f01[VEC], f10[VEC], f11[VEC];
+                    widen(q00[n], f00, FT());
+                    widen(q01[n], f01, FT());
+                    widen(q10[n], f10, FT());
+                    widen(q11[n], f11, FT());
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        float a = acc[n * VEC + j];
+                        a = fmaf(w00, f00[j], a);
+                        a = fmaf(w01, f01[j], a);
+                        a = fmaf(w10, f10[j], a);
+                        a = fmaf(w11, f11[j], a);
+                        acc[n * VEC + j] = a;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Sum the teams' partial rows in team order and write out[row] (n = C values).
+__device__ __forceinline__ void reduce_and_store(const float* spart, int nteams, int C, void* out,
+                                                 int out_t, long long orow) {
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float v = spart[c];
+        for (int t = 1; t < nteams; ++t) v += spart[(size_t)t * C + c];
+        const long long o = orow * C + c;
+        if (out_t == MSDA_F32)
+            store_out(reinterpret_cast<float*>(out) + o, v);
+        else if (out_t == MSDA_BF16)
+            store_out(reinterpret_cast<__nv_bfloat16*>(out) + o, v);
+        else
+            store_out(reinterpret_cast<__half*>(out) + o, v);
+    }
+}
+
+template <typename FT, typename WT, int NV>
+__global__ void __launch_bounds__(512) fwd_anchor_kernel(const FwdArgs p) {
+    constexpr int CPL = Elem<FT>::VEC * NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nmaps = p.Ncam * p.Nscale;
+    const int tpw = 32 / p.rt;
+    const int nteams = (blockDim.x >> 5) * tpw;
+    const FwdSmem lay(nmaps, p.P, p.Ncam, nteams, p.C);
+    MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
+    float2* sloc = reinterpret_cast<float2*>(smem + lay.loc);
+    float* spart = reinterpret_cast<float*>(smem + lay.part);
+
+    const long long ba = blockIdx.x;
+    const int b = (int)(ba / p.A);
+    for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
+        smap[i] = load_map(p.shape, p.start, i, p.sum_hw, p.status);
+    const float2* gloc = reinterpret_cast<const float2*>(p.loc) + ba * (long long)(p.P * p.Ncam);
+    for (int i = threadIdx.x; i < p.P * p.Ncam; i += blockDim.x) sloc[i] = __ldg(gloc + i);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int team = (threadIdx.x >> 5) * tpw + lane / p.rt;
+    const int c0 = (lane & (p.rt - 1)) * CPL;
+    const int g = c0 / p.Cg;
+    const FT* fb = reinterpret_cast<const FT*>(p.feat) + (long long)b * p.sum_hw * p.C + c0;
+    const WT* wb = reinterpret_cast<const WT*>(p.w) + ba * ((long long)p.P * p.Ncam * p.Nscale * p.G) + g;
+
+    float acc[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) acc[j] = 0.0f;
+    accumulate_anchor<FT, WT, NV>(fb, wb, smap, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc);
+
+    float* mine = spart + (size_t)team * p.C + c0;
+#pragma unroll
+    for (int j = 0; j < CPL; j += 4) *reinterpret_cast<float4*>(mine + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    __syncthreads();
+    reduce_and_store(spart, nteams, p.C, p.out, p.out_t, ba);
+}
+
+// ---------------------------------------------------------------------------
+// Batched serving: one persistent launch over all scenes' anchors.
+//
+// Work units are anchors, numbered scene by scene (unit_begin).  Each
+// resident block pulls the next unit from an atomic counter, so large and
+// small scenes interleave and the tail stays short.  The scene of a unit is
+// found by binary search over unit_begin.  When a block finishes the last
+// anchor of a scene (per-scene counter), it stamps %globaltimer into
+// done_ns[scene + 1]; block 0 stamps the start into done_ns[0].  No block
+// waits on another.
+// ---------------------------------------------------------------------------
+struct BatchedArgs {
+    const msda_scene* scenes;
+    int num_scenes, total;
+    int max_ncam, Nscale, C, P, G, Cg, rt, out_t;
+    unsigned int* counters;  // [0] = next unit, [1 + i] = finished anchors of scene i
+    uint64_t* done_ns;
+    int* status;
+};
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename FT, typename WT, int NV>
+__global__ void __launch_bounds__(512) fwd_batched_kernel(const BatchedArgs p) {
+    constexpr int CPL = Elem<FT>::VEC * NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tpw = 32 / p.rt;
+    const int nteams = (blockDim.x >> 5) * tpw;
+    const FwdSmem lay(p.max_ncam * p.Nscale, p.P, p.max_ncam, nteams, p.C);
+    MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
+    float2* sloc = reinterpret_cast<float2*>(smem + lay.loc);
+    float* spart = reinterpret_cast<float*>(smem + lay.part);
+    __shared__ int s_unit, s_scene;
+
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.done_ns) p.done_ns[0] = globaltimer();
+    const int lane = threadIdx.x & 31;
+    const int team = (threadIdx.x >> 5) * tpw + lane / p.rt;
+    const int c0 = (lane & (p.rt - 1)) * CPL;
+    const int g = c0 / p.Cg;
+    int cur_scene = -1;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int u = (int)atomicAdd(p.counters, 1u);
+            int sc = -1;
+            if (u < p.total) {
+                int lo = 0, hi = p.num_scenes - 1;  // last scene with unit_begin <= u
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (p.scenes[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+                }
+                sc = lo;
+            }
+            s_unit = u;
+            s_scene = sc;
+        }
+        __syncthreads();
+        const int u = s_unit, sc = s_scene;
+        if (u >= p.total) break;
+        const msda_scene S = p.scenes[sc];
+        const int a = u - S.unit_begin;
+        const int ncam = S.Ncam;
+        bool bad = (ncam > p.max_ncam || ncam < 0 || a >= S.A);
+        if (bad) {
+            if (threadIdx.x == 0) raise_status(p.status, MSDA_ERR_OUT_OF_RANGE);
+        } else {
+            if (sc != cur_scene) {
+                for (int i = threadIdx.x; i < ncam * p.Nscale; i += blockDim.x)
+                    smap[i] = load_map(S.spatial_shape, S.scale_start_index, i, S.sum_hw, p.status);
+            }
+            const float2* gloc = reinterpret_cast<const float2*>(S.sampling_location) + (long long)a * (p.P * ncam);
+            for (int i = threadIdx.x; i < p.P * ncam; i += blockDim.x) sloc[i] = __ldg(gloc + i);
+            __syncthreads();
+            const FT* fb = reinterpret_cast<const FT*>(S.feat) + c0;
+            const WT* wb = reinterpret_cast<const WT*>(S.weights) + (long long)a * ((long long)p.P * ncam * p.Nscale * p.G) + g;
+            float acc[CPL];
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) acc[j] = 0.0f;
+            accumulate_anchor<FT, WT, NV>(fb, wb, smap, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc);
+            float* mine = spart + (size_t)team * p.C + c0;
+#pragma unroll
+            for (int j = 0; j < CPL; j += 4) *reinterpret_cast<float4*>(mine + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+            __syncthreads();
+            reduce_and_store(spart, nteams, p.C, S.out, p.out_t, a);
+            cur_scene = sc;
+        }
+        __syncthreads();  // partial rows, staged tables and s_unit are reused next round
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned int done = atomicAdd(p.counters + 1 + sc, 1u) + 1u;
+            if (!bad && done == (unsigned int)S.A && p.done_ns) p.done_ns[1 + sc] = globaltimer();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+using FwdKernel = void (*)(const FwdArgs);
+using BatchedKernel = void (*)(const BatchedArgs);
+
+template <typename FT, typename WT>
+static FwdKernel fwd_pick_nv(int nv) {
+    switch (nv) {
+        case 1: return fwd_anchor_kernel<FT, WT, 1>;
+        case 2: return fwd_anchor_kernel<FT, WT, 2>;
+        case 4: return fwd_anchor_kernel<FT, WT, 4>;
+    }
+    return nullptr;
+}
+
+template <typename FT, typename WT>
+static BatchedKernel batched_pick_nv(int nv) {
+    switch (nv) {
+        case 1: return fwd_batched_kernel<FT, WT, 1>;
+        case 2: return fwd_batched_kernel<FT, WT, 2>;
+        case 4: return fwd_batched_kernel<FT, WT, 4>;
+    }
+    return nullptr;
+}
+
+// Supported (feature, weight) dtype pairs: weights in FP32 or in the feature dtype.
+static FwdKernel fwd_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
+    if (ft == MSDA_F32 && wt == MSDA_F32) return fwd_pick_nv<float, float>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_BF16) return fwd_pick_nv<__nv_bfloat16, __nv_bfloat16>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_F32) return fwd_pick_nv<__nv_bfloat16, float>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F16) return fwd_pick_nv<__half, __half>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F32) return fwd_pick_nv<__half, float>(nv);
+    return nullptr;
+}
+
+static BatchedKernel batched_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
+    if (ft == MSDA_F32 && wt == MSDA_F32) return batched_pick_nv<float, float>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_BF16) return batched_pick_nv<__nv_bfloat16, __nv_bfloat16>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_F32) return batched_pick_nv<__nv_bfloat16, float>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F16) return batched_pick_nv<__half, __half>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F32) return batched_pick_nv<__half, float>(nv);
+    return nullptr;
+}
+
+msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int warps,
+                           cudaStream_t stream) {
+    DeviceInfo dev;
+    msda_status st = device_info(&dev);
+    if (st != MSDA_OK) return st;
+    FwdKernel k = fwd_kernel_for(p.feat_t, p.w_t, p.nv);
+    if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: unsupported feature/weight dtype pair");
+    const long long nblocks = (long long)p.B * p.A;
+    if (nblocks == 0) return MSDA_OK;
+    if (nblocks > 0x7fffffffLL) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: B*A too large");
+    const int nteams = warps * (32 / p.rt);
+    const FwdSmem lay(p.Ncam * p.Nscale, p.P, p.Ncam, nteams, p.C);
+    st = ensure_smem((const void*)k, lay.total, dev);
+    if (st != MSDA_OK) return st;
+    FwdArgs a;
+    a.feat = p.feat; a.shape = p.shape; a.start = p.start; a.loc = p.loc; a.w = p.w;
+    a.out = out; a.out_t = out_t;
+    a.B = p.B; a.sum_hw = p.sum_hw; a.C = p.C; a.Ncam = p.Ncam; a.Nscale = p.Nscale;
+    a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.status = dev.status;
+    k<<<(unsigned)nblocks, warps * 32, lay.total, stream>>>(a);
+    return check_launch("msda_forward");
+}
+
+size_t batched_workspace(int num_scenes) { return align_up(sizeof(unsigned int) * (size_t)(num_scenes + 1), 256); }
+
+msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int total_anchors,
+                                   int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,
+                                   msda_dtype wt, msda_dtype ot, void* ws, size_t ws_bytes,
+                                   uint64_t* done_ns, int warps, int blocks_per_sm,
+                                   cudaStream_t stream) {
+    DeviceInfo dev;
+    msda_status st = device_info(&dev);
+    if (st != MSDA_OK) return st;
+    int nv, rt;
+    if (!pick_split(C, G, ft, &nv, &rt))
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_batched: no lane split for C=%d G=%d", C, G);
+    BatchedKernel k = batched_kernel_for(ft, wt, nv);
+    if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_batched: unsupported dtype pair");
+    const size_t need = batched_workspace(num_scenes);
+    if (!ws || ws_bytes < need)
+        return fail(MSDA_ERR_WORKSPACE, "msda_forward_batched: workspace needs %zu bytes", need);
+    const int nteams = warps * (32 / rt);
+    const FwdSmem lay(max_ncam * Nscale, P, max_ncam, nteams, C);
+    st = ensure_smem((const void*)k, lay.total, dev);
+    if (st != MSDA_OK) return st;
+    if (cudaMemsetAsync(ws, 0, need, stream) != cudaSuccess) return check_launch("msda_forward_batched memset");
+    if (total_anchors == 0) return MSDA_OK;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, warps * 32, lay.total) != cudaSuccess || occ < 1)
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_batched: kernel does not fit on an SM");
+    const int per_sm = blocks_per_sm > 0 ? (blocks_per_sm < occ ? blocks_per_sm : occ) : occ;
+    long long grid = (long long)per_sm * dev.sm_count;
+    if (grid > total_anchors) grid = total_anchors;
+    BatchedArgs a;
+    a.scenes = scenes; a.num_scenes = num_scenes; a.total = total_anchors;
+    a.max_ncam = max_ncam; a.Nscale = Nscale; a.C = C; a.P = P; a.G = G; a.Cg = C / G;
+    a.rt = rt; a.out_t = ot; a.counters = reinterpret_cast<unsigned int*>(ws);
+    a.done_ns = done_ns; a.status = dev.status;
+    k<<<(unsigned)grid, warps * 32, lay.total, stream>>>(a);
+    return check_launch("msda_forward_batched");
+}
+
+}  // namespace msda

@@ -1,0 +1,148 @@
+"""Backward parity: atomic and deterministic modes against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import (TOL_FP32, TOL_LOWP_GRAD, ensure_lib, is_lowp, oracle_backward, relerr)
+from paper_2601_10819_gb300 import inputs, msda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    oracle.build()
+    return ensure_lib()
+
+
+def gpu_backward(pr, deterministic, warps=None):
+    d = pr.to("cuda")
+    g = msda.backward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights, d.grad_out,
+                      deterministic=deterministic, warps=warps)
+    torch.cuda.synchronize()
+    return [t.cpu() for t in g]
+
+
+def check_against_oracle(pr, grads, tol, label=""):
+    ref = oracle_backward(pr)
+    errs = [relerr(g.double().numpy(), r) for g, r in zip(grads, ref)]
+    print(f"{label} rel err dfeat {errs[0]:.2e} dloc {errs[1]:.2e} dw {errs[2]:.2e}")
+    assert max(errs) <= tol, errs
+    return errs
+
+
+@pytest.mark.parametrize("det", [False, True])
+@pytest.mark.parametrize("warps", [1, 4, 8])
+def test_tiny_fp32(det, warps):
+    pr = inputs.make_workload(0)
+    check_against_oracle(pr, gpu_backward(pr, det, warps), TOL_FP32, f"tiny det={det} warps={warps}")
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_sparse4d_fp32_subset(det):
+    pr = inputs.make_workload(1).anchors(range(150))
+    check_against_oracle(pr, gpu_backward(pr, det), TOL_FP32, f"sparse4d fp32 det={det}")
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_train_16cam_bf16_subset(det):
+    pr = inputs.make_workload(3, batch=2).anchors(range(120))
+    check_against_oracle(pr, gpu_backward(pr, det), TOL_LOWP_GRAD, f"train bf16 det={det}")
+
+
+HETERO = [[(5, 7), (3, 4), (2, 2)], [(9, 4), (4, 2), (1, 1)], [(6, 13), (3, 7), (2, 3)]]
+
+
+@pytest.mark.parametrize("C,G,fdt", [(32, 4, "f32"), (64, 8, "bf16"), (128, 2, "f16"), (512, 8, "bf16")])
+@pytest.mark.parametrize("det", [False, True])
+def test_ragged_maps_and_splits(C, G, fdt, det):
+    gen = torch.Generator().manual_seed(C + G)
+    pr = inputs.make_problem(gen, B=2, cam_maps=HETERO, C=C, G=G, A=23, P=5, loc_range=(-0.3, 1.3),
+                             feat_dtype=fdt, w_dtype=fdt)
+    tol = TOL_FP32 if not is_lowp(pr) else TOL_LOWP_GRAD
+    check_against_oracle(pr, gpu_backward(pr, det), tol, f"ragged C={C} G={G} {fdt} det={det}")
+
+
+def test_deterministic_mode_is_bitwise_reproducible():
+    pr = inputs.make_workload(2, ncam=8)
+    a = gpu_backward(pr, True, warps=8)
+    b = gpu_backward(pr, True, warps=8)
+    c = gpu_backward(pr, True, warps=4)
+    for x, y, z in zip(a, b, c):
+        assert torch.equal(x, y)
+        assert torch.equal(x, z)  # every gradient is computed in a fixed order independent of the warps
+
+
+def test_atomic_mode_matches_deterministic():
+    pr = inputs.make_workload(2, ncam=8)
+    a = gpu_backward(pr, False)
+    d = gpu_backward(pr, True)
+    assert torch.equal(a[1], d[1]) and torch.equal(a[2], d[2])  # dloc, dw: same kernel, no atomics
+    assert relerr(a[0].double().numpy(), d[0].double().numpy()) <= 1e-6
+
+
+def test_outside_in_64cam_full_backward():
+    """The benchmark's workload: every gradient against the oracle at full size."""
+    pr = inputs.make_workload(2)
+    ga = gpu_backward(pr, False)
+    ref = oracle_backward(pr)
+    for g, r, name in zip(ga, ref, ["dfeat", "dloc", "dw"]):
+        e = relerr(g.double().numpy(), r)
+        print(f"outside-in-64cam {name} rel err {e:.2e}")
+        assert e <= TOL_LOWP_GRAD
+    gd = gpu_backward(pr, True)
+    assert relerr(gd[0].double().numpy(), ref[0]) <= TOL_LOWP_GRAD
+
+
+def test_train_16cam_full_adjoint_and_sampled_anchors():
+    """Full size B=4 x 16 cameras: adjoint identities plus exact per-anchor checks on sampled anchors."""
+    pr = inputs.make_workload(3)
+    d = pr.to("cuda")
+    out = msda.forward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    gf, gl, gw = msda.backward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights,
+                               d.grad_out)
+    lhs = float((d.grad_out.double() * out.double()).sum())
+    assert abs(lhs - float((gf.double() * d.feat.double()).sum())) <= 1e-4 * abs(lhs)
+    assert abs(lhs - float((gw.double() * d.weights.double()).sum())) <= 1e-4 * abs(lhs)
+    idx = torch.randperm(900, generator=torch.Generator().manual_seed(0))[:24]
+    sub = pr.anchors(idx)
+    _, rl, rw = oracle_backward(sub)
+    assert relerr(gl.cpu()[:, idx].double().numpy(), rl) <= TOL_LOWP_GRAD
+    assert relerr(gw.cpu()[:, idx].double().numpy(), rw) <= TOL_LOWP_GRAD
+
+
+def test_autograd_function_matches_direct_calls_and_gradcheck():
+    pr = inputs.make_workload(0)
+    d = pr.to("cuda")
+    feat = d.feat.clone().requires_grad_()
+    loc = d.sampling_location.clone().requires_grad_()
+    w = d.weights.clone().requires_grad_()
+    out = msda.msda(feat, d.spatial_shape, d.scale_start_index, loc, w)
+    out.backward(d.grad_out)
+    gf, gl, gw = msda.backward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights,
+                               d.grad_out)
+    assert torch.equal(w.grad, gw) and torch.equal(loc.grad, gl)  # no atomics: bitwise
+    assert relerr(feat.grad.cpu().double().numpy(), gf.cpu().double().numpy()) <= 1e-6  # atomic order varies
+    # the operator is linear in feat and weights: finite differences are exact up to rounding
+    f0 = d.feat.clone().requires_grad_()
+    w0 = d.weights.clone().requires_grad_()
+    fn = lambda f, ww: msda.msda(f, d.spatial_shape, d.scale_start_index, d.sampling_location, ww)
+    assert torch.autograd.gradcheck(fn, (f0, w0), eps=1e-2, atol=2e-3, rtol=1e-2, fast_mode=True)
+
+
+def test_out_of_view_points_have_zero_gradients():
+    pr = inputs.make_workload(0)
+    pr.sampling_location[0, :5, :, :, 0] = 3.0
+    gf, gl, gw = gpu_backward(pr, False)
+    assert torch.all(gl[0, :5] == 0) and torch.all(gw[0, :5] == 0)
+    check_against_oracle(pr, (gf, gl, gw), TOL_FP32, "out of view")
+
+
+def test_empty_backward():
+    gen = torch.Generator().manual_seed(0)
+    pr = inputs.make_problem(gen, B=1, cam_maps=[[(4, 4)]], C=32, G=4, A=0, P=2)
+    for det in (False, True):
+        gf, gl, gw = gpu_backward(pr, det)
+        assert torch.all(gf == 0) and gl.numel() == 0 and gw.numel() == 0
