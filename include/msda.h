@@ -79,7 +79,7 @@ typedef enum { MSDA_F32 = 0, MSDA_BF16 = 1, MSDA_F16 = 2 } msda_dtype;
  * different tunings may differ in the last bits, because the warps_per_block
  * split decides the order of the FP32 sums. */
 typedef struct {
-    int warps_per_block;   /* 1..16: warps cooperating on one anchor             */
+    int warps_per_block;   /* 1..8: warps per block (teams of lanes per block)   */
     int blocks_per_sm;     /* persistent batched kernel: resident blocks per SM  */
     int reserved[6];
 } msda_tuning;

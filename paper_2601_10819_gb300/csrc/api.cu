@@ -93,7 +93,7 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 static int pick_warps(const msda_tuning* t, int dflt) {
     const int w = (t && t->warps_per_block > 0) ? t->warps_per_block : dflt;
-    return w > 16 ? 16 : w;
+    return w > 8 ? 8 : w;
 }
 
 // Shared validation of the single-scene entry points.

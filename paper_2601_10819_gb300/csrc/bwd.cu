@@ -8,13 +8,18 @@
 // (the paper's operator is an inference plugin, Sec. 5.3; this is the
 // exact adjoint of the forward).
 //
-// Mapping: as in the forward, one block per anchor and one team of rt lanes
-// per (camera, keypoint) item, each lane owning CPL contiguous channels.  The
-// lane keeps its slice of go in registers for the whole anchor.  One pass
-// over the item re-reads the four corners, reduces dw over the group's lanes
-// and du/dv over the team with shuffles (fixed trees, no atomics: those two
-// gradients are bitwise reproducible), and scatters the feature gradient
-// with 16-byte FP32 vector atomics (red.global.add.v4.f32).
+// Mapping: a persistent grid whose teams (rt lanes, each owning CPL
+// contiguous channels) walk ONE global list of (camera, anchor, keypoint)
+// items in camera-major order: team j of the whole grid takes items j,
+// j + teams, ...  At any moment every team works inside the same fraction of
+// one camera, so that camera's features and its FP32 feature-gradient rows
+// stay in L2 while they are hit, and the work is balanced to one item.  One
+// pass over an item reads its four corners per scale, reduces dw over the
+// group's lanes and du/dv over the team with shuffles (fixed trees, no
+// atomics: those two gradients are bitwise reproducible and independent of
+// the launch shape), and scatters the feature gradient with 16-byte FP32
+// vector atomics (red.global.add.v4.f32) in an interleaved lane layout, so
+// each warp-wide atomic covers whole 32-byte sectors.
 #include "common.cuh"
 #include "internal.h"
 
@@ -46,20 +51,14 @@ __device__ __forceinline__ float team_sum(float v, unsigned mask, int width) {
 }
 
 template <typename FT, typename WT, int NV>
-__global__ void __launch_bounds__(512) bwd_atomic_kernel(const BwdArgs p) {
+__global__ void __launch_bounds__(256, NV == 1 ? 4 : 2) bwd_atomic_kernel(const BwdArgs p) {
     constexpr int VEC = Elem<FT>::VEC;
     constexpr int CPL = VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nmaps = p.Ncam * p.Nscale;
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem);
-    float2* sloc = reinterpret_cast<float2*>(smem + align16(sizeof(MapInfo) * (size_t)nmaps));
-
-    const long long ba = blockIdx.x;
-    const int b = (int)(ba / p.A);
     for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
         smap[i] = load_map(p.shape, p.start, i, p.sum_hw, p.status);
-    const float2* gl = reinterpret_cast<const float2*>(p.loc) + ba * (long long)(p.P * p.Ncam);
-    for (int i = threadIdx.x; i < p.P * p.Ncam; i += blockDim.x) sloc[i] = __ldg(gl + i);
     __syncthreads();
 
     const int tpw = 32 / p.rt;
@@ -69,34 +68,37 @@ __global__ void __launch_bounds__(512) bwd_atomic_kernel(const BwdArgs p) {
     const int team = (threadIdx.x >> 5) * tpw + tiw;
     const int tl = lane & (p.rt - 1);
     const unsigned tmask = (p.rt == 32) ? 0xffffffffu : (((1u << p.rt) - 1u) << (tiw * p.rt));
-    const int c0 = tl * CPL;
+    const int c0 = tl * CPL;          // contiguous channels of this lane (loads, dw, dloc)
     const int g = c0 / p.Cg;
-    const int lg = p.Cg / CPL;  // lanes per group (power of two)
+    const int lg = p.Cg / CPL;        // lanes per group (power of two)
+    const int ci = 4 * tl;            // interleaved channels of this lane (scatter): ci + j*4*rt
+    const int cstride = 4 * p.rt;
 
-    const FT* fb = reinterpret_cast<const FT*>(p.feat) + (long long)b * p.sum_hw * p.C + c0;
-    float* gfb = p.gfeat + (long long)b * p.sum_hw * p.C + c0;
-    const long long wanchor = ba * ((long long)p.P * p.Ncam * p.Nscale * p.G);
-    const WT* wb = reinterpret_cast<const WT*>(p.w) + wanchor + g;
-    float* gwb = p.gw + wanchor + g;
-
-    float go[CPL];
-    {
-        const float4* gsrc = reinterpret_cast<const float4*>(p.go + ba * p.C + c0);
+    const long long BA = (long long)p.B * p.A;
+    const long long per_cam = BA * p.P;
+    const long long nitems = (long long)p.Ncam * per_cam;
+    const long long total_teams = (long long)gridDim.x * nteams;
+    // Global item list ordered (camera, anchor, keypoint); all teams walk it together.
+    for (long long item = (long long)blockIdx.x * nteams + team; item < nitems; item += total_teams) {
+        const int k = (int)(item / per_cam);
+        const long long r = item - (long long)k * per_cam;
+        const long long ba = r / p.P;
+        const int pp = (int)(r - ba * p.P);
+        const int b = (int)(ba / p.A);
+        const long long pk = (ba * p.P + pp) * p.Ncam + k;
+        const float2 uv = __ldg(reinterpret_cast<const float2*>(p.loc) + pk);
+        const float* gorow = p.go + ba * p.C;
+        float go[CPL];
 #pragma unroll
         for (int j = 0; j < CPL / 4; ++j) {
-            const float4 t = __ldg(gsrc + j);
+            const float4 t = __ldg(reinterpret_cast<const float4*>(gorow + c0) + j);
             go[4 * j + 0] = t.x; go[4 * j + 1] = t.y; go[4 * j + 2] = t.z; go[4 * j + 3] = t.w;
         }
-    }
-
-    const int nitems = p.Ncam * p.P;
-    for (int item = team; item < nitems; item += nteams) {
-        const int k = item / p.P;
-        const int pp = item - k * p.P;
-        const float2 uv = sloc[pp * p.Ncam + k];
-        const long long pk = (long long)pp * p.Ncam + k;
-        const WT* wrow = wb + pk * p.Nscale * p.G;
-        float* gwrow = gwb + pk * p.Nscale * p.G;
+        const FT* fb = reinterpret_cast<const FT*>(p.feat) + (long long)b * p.sum_hw * p.C + c0;
+        float* gfb = p.gfeat + (long long)b * p.sum_hw * p.C + ci;
+        const WT* wpt = reinterpret_cast<const WT*>(p.w) + pk * p.Nscale * p.G;  // weights of this point
+        const WT* wrow = wpt + g;
+        float* gwrow = p.gw + pk * p.Nscale * p.G + g;
         const MapInfo* mrow = smap + k * p.Nscale;
         float du = 0.0f, dv = 0.0f;
         for (int s = 0; s < p.Nscale; ++s) {
@@ -141,17 +143,21 @@ __global__ void __launch_bounds__(512) bwd_atomic_kernel(const BwdArgs p) {
                 }
                 du = fmaf((float)m.W * wv, gxp, du);
                 dv = fmaf((float)m.H * wv, gyp, dv);
-                // feature gradient: w * omega * go for each in-bound corner
                 if (p.scatter) {
+                    // feature gradient w * omega * go, in the interleaved layout: each warp-wide
+                    // 16-byte vector atomic covers 4*rt contiguous channels (whole sectors)
+                    // (an interleaved chunk belongs to its own group, with its own weight)
                     float* g00 = gfb + r00;
-                    const float c00 = wv * o00, c01 = wv * o01, c10 = wv * o10, c11 = wv * o11;
 #pragma unroll
-                    for (int j = 0; j < CPL; j += 4) {
-                        const float4 gv = make_float4(go[j], go[j + 1], go[j + 2], go[j + 3]);
-                        if (vy0 && vx0) atomicAdd(reinterpret_cast<float4*>(g00 + j), scale4(c00, gv));
-                        if (vy0 && vx1) atomicAdd(reinterpret_cast<float4*>(g00 + p.C + j), scale4(c01, gv));
-                        if (vy1 && vx0) atomicAdd(reinterpret_cast<float4*>(g00 + rW + j), scale4(c10, gv));
-                        if (vy1 && vx1) atomicAdd(reinterpret_cast<float4*>(g00 + rW + p.C + j), scale4(c11, gv));
+                    for (int j = 0; j < CPL / 4; ++j) {
+                        const float wj = ldw(wpt + (long long)s * p.G + (ci + j * cstride) / p.Cg);
+                        const float c00 = wj * o00, c01 = wj * o01, c10 = wj * o10, c11 = wj * o11;
+                        const float4 gv = __ldg(reinterpret_cast<const float4*>(gorow + ci + j * cstride));
+                        float* q = g00 + j * cstride;
+                        if (vy0 && vx0) atomicAdd(reinterpret_cast<float4*>(q), scale4(c00, gv));
+                        if (vy0 && vx1) atomicAdd(reinterpret_cast<float4*>(q + p.C), scale4(c01, gv));
+                        if (vy1 && vx0) atomicAdd(reinterpret_cast<float4*>(q + rW), scale4(c10, gv));
+                        if (vy1 && vx1) atomicAdd(reinterpret_cast<float4*>(q + rW + p.C), scale4(c11, gv));
                     }
                 }
             }
@@ -161,10 +167,7 @@ __global__ void __launch_bounds__(512) bwd_atomic_kernel(const BwdArgs p) {
         }
         du = team_sum(du, tmask, p.rt);
         dv = team_sum(dv, tmask, p.rt);
-        if (tl == 0) {
-            float2* dst = reinterpret_cast<float2*>(p.gloc) + (ba * p.P + pp) * p.Ncam + k;
-            *dst = make_float2(du, dv);
-        }
+        if (tl == 0) reinterpret_cast<float2*>(p.gloc)[pk] = make_float2(du, dv);
     }
 }
 
@@ -189,9 +192,7 @@ static BwdKernel bwd_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
     return nullptr;
 }
 
-size_t bwd_smem_bytes(const Problem& p) {
-    return align16(sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale) + sizeof(float2) * (size_t)p.P * p.Ncam;
-}
+size_t bwd_smem_bytes(const Problem& p) { return sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale; }
 
 msda_status launch_backward_atomic(const Problem& p, const float* grad_out, float* grad_feat,
                                    float* grad_loc, float* grad_w, int warps, cudaStream_t stream) {
@@ -219,7 +220,17 @@ msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float
     a.go = grad_out; a.gfeat = grad_feat; a.gloc = grad_loc; a.gw = grad_w;
     a.B = p.B; a.sum_hw = p.sum_hw; a.C = p.C; a.Ncam = p.Ncam; a.Nscale = p.Nscale;
     a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.scatter = scatter; a.status = dev.status;
-    k<<<(unsigned)nblocks, warps * 32, smem, stream>>>(a);
+    // persistent grid: as many blocks as fit at once, all walking one camera-major item list
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, warps * 32, smem) != cudaSuccess || occ < 1)
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: kernel does not fit on an SM");
+    const long long items = (long long)p.Ncam * nblocks * p.P;
+    const int nteams = warps * (32 / p.rt);
+    long long grid = (long long)occ * dev.sm_count;
+    const long long needed = (items + nteams - 1) / nteams;
+    if (grid > needed) grid = needed;
+    if (grid < 1) grid = 1;
+    k<<<(unsigned)grid, warps * 32, smem, stream>>>(a);
     return check_launch("msda_backward");
 }
 

@@ -136,7 +136,7 @@ __device__ __forceinline__ void reduce_and_store(const float* spart, int nteams,
 }
 
 template <typename FT, typename WT, int NV>
-__global__ void __launch_bounds__(512) fwd_anchor_kernel(const FwdArgs p) {
+__global__ void __launch_bounds__(256, NV == 1 ? 6 : 3) fwd_anchor_kernel(const FwdArgs p) {
     constexpr int CPL = Elem<FT>::VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nmaps = p.Ncam * p.Nscale;

@@ -128,7 +128,7 @@ def test_autograd_function_matches_direct_calls_and_gradcheck():
     # the operator is linear in feat and weights: finite differences are exact up to rounding
     f0 = d.feat.clone().requires_grad_()
     w0 = d.weights.clone().requires_grad_()
-    fn = lambda f, ww: msda.msda(f, d.spatial_shape, d.scale_start_index, d.sampling_location, ww)
+    fn = lambda f, ww: msda.msda(f, d.spatial_shape, d.scale_start_index, d.sampling_location, ww, True)
     assert torch.autograd.gradcheck(fn, (f0, w0), eps=1e-2, atol=2e-3, rtol=1e-2, fast_mode=True)
 
 
