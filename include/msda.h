@@ -178,6 +178,33 @@ msda_status msda_forward_batched(const msda_scene* scenes, int num_scenes, int t
                                  const msda_tuning* tuning, msda_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * msda_forward_batched_noalloc - msda_forward_batched without a workspace.
+ * The paper has no counterpart; this exists for callers that cannot
+ * allocate device memory where they launch work (a plugin's enqueue inside
+ * an inference engine, a real-time loop with a fixed memory budget, a C host
+ * program without a device allocator).  Same arguments and results as
+ * msda_forward_batched minus the workspace: the scratch is a device array
+ * built into the library, sized for at most
+ * msda_forward_batched_noalloc_max_scenes() scenes (1024); more scenes are
+ * rejected with MSDA_ERR_INVALID_ARG.  The call allocates nothing (no
+ * cudaMalloc/cudaFree, no allocating library routine).  Every GPU that
+ * loads the library keeps the array until the process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the array and each call clears it first, so calls
+ *     that overlap on the GPU (different streams, no ordering between them)
+ *     race and give wrong results: order them on one stream or with events.
+ * ------------------------------------------------------------------------ */
+int msda_forward_batched_noalloc_max_scenes(void);
+
+msda_status msda_forward_batched_noalloc(const msda_scene* scenes, int num_scenes, int total_anchors,
+                                         int max_ncam, int Nscale, int C, int P, int G,
+                                         msda_dtype feat_dtype, msda_dtype weights_dtype,
+                                         msda_dtype out_dtype, uint64_t* scene_done_ns,
+                                         const msda_tuning* tuning, msda_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Status and diagnostics
  * ------------------------------------------------------------------------ */
 /* Synchronises `stream`, returns the device status word of the current

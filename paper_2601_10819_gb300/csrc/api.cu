@@ -222,6 +222,34 @@ msda_status msda_forward_batched(const msda_scene* scenes, int num_scenes, int t
                                   (cudaStream_t)stream);
 }
 
+int msda_forward_batched_noalloc_max_scenes(void) { return batched_noalloc_max_scenes(); }
+
+msda_status msda_forward_batched_noalloc(const msda_scene* scenes, int num_scenes, int total_anchors,
+                                         int max_ncam, int Nscale, int C, int P, int G, msda_dtype feat_dtype,
+                                         msda_dtype weights_dtype, msda_dtype out_dtype, uint64_t* scene_done_ns,
+                                         const msda_tuning* tuning, msda_stream_t stream) {
+    t_err[0] = 0;
+    const char* fn = "msda_forward_batched_noalloc";
+    if (num_scenes < 0 || total_anchors < 0 || max_ncam < 0 || Nscale < 0 || P < 0)
+        return fail(MSDA_ERR_INVALID_ARG, "%s: negative dimension", fn);
+    if (num_scenes > batched_noalloc_max_scenes())
+        return fail(MSDA_ERR_INVALID_ARG, "%s: %d scenes exceed the built-in limit of %d", fn, num_scenes,
+                    batched_noalloc_max_scenes());
+    if (C < 1 || G < 1 || C % G) return fail(MSDA_ERR_INVALID_ARG, "%s: need C %% G == 0", fn);
+    if (Nscale > kMaxScales) return fail(MSDA_ERR_UNSUPPORTED, "%s: Nscale too large", fn);
+    if (dtype_size(feat_dtype) == 0 || dtype_size(weights_dtype) == 0 || dtype_size(out_dtype) == 0)
+        return fail(MSDA_ERR_INVALID_ARG, "%s: unknown dtype", fn);
+    if ((C / G) * dtype_size(feat_dtype) % 16 != 0)
+        return fail(MSDA_ERR_UNSUPPORTED, "%s: (C/G)*sizeof(feat) not a multiple of 16", fn);
+    if (num_scenes > 0 && !scenes) return fail(MSDA_ERR_INVALID_ARG, "%s: scenes is NULL", fn);
+    if (num_scenes == 0 && total_anchors > 0) return fail(MSDA_ERR_INVALID_ARG, "%s: anchors without scenes", fn);
+    if (!aligned16(scenes) || !aligned16(scene_done_ns))
+        return fail(MSDA_ERR_UNSUPPORTED, "%s: pointers must be 16-byte aligned", fn);
+    return launch_forward_batched_noalloc(scenes, num_scenes, total_anchors, max_ncam, Nscale, C, P, G, feat_dtype,
+                                          weights_dtype, out_dtype, scene_done_ns, pick_warps(tuning, 8),
+                                          tuning ? tuning->blocks_per_sm : 0, (cudaStream_t)stream);
+}
+
 msda_status msda_get_device_status(msda_stream_t stream) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);

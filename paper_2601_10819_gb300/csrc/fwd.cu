@@ -22,6 +22,8 @@
 // Accumulation is FP32 in registers in a fixed order; the teams' partial
 // rows are summed in team order through shared memory, so a given launch
 // configuration is bitwise reproducible.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -378,6 +380,57 @@ msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int
     a.done_ns = done_ns; a.status = dev.status;
     k<<<(unsigned)grid, warps * 32, lay.total, stream>>>(a);
     return check_launch("msda_forward_batched");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched forward.
+//
+// Some callers cannot allocate device memory at the point where they launch
+// work: a plugin's enqueue inside an inference engine, a real-time serving
+// loop with a fixed memory budget, or a plain C host program that links only
+// this library and has no device allocator of its own.  For them the batched
+// forward's scratch (one work counter plus one finished-anchor counter per
+// scene) lives in this file-scope device array instead of a caller workspace.
+// Every GPU that loads the library holds the array until the process exits.
+// Host code cannot use the array's name as a device address, so its address
+// is looked up once per device (the device being current) with
+// cudaGetSymbolAddress and passed to the kernel.  The counters are cleared by
+// every call; calls share them, so two calls that overlap on the GPU (on
+// different streams without ordering) race and give wrong results.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxScenes = 1024;
+static __device__ __align__(256) unsigned int g_batched_noalloc_scratch[kNoAllocMaxScenes + 1];
+
+int batched_noalloc_max_scenes() { return kNoAllocMaxScenes; }
+
+msda_status launch_forward_batched_noalloc(const msda_scene* scenes, int num_scenes, int total_anchors,
+                                           int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,
+                                           msda_dtype wt, msda_dtype ot, uint64_t* done_ns, int warps,
+                                           int blocks_per_sm, cudaStream_t stream) {
+    if (num_scenes > kNoAllocMaxScenes)
+        return fail(MSDA_ERR_INVALID_ARG, "msda_forward_batched_noalloc: %d scenes exceed the built-in limit of %d",
+                    num_scenes, kNoAllocMaxScenes);
+    static std::mutex mu;
+    static void* addr[128];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(MSDA_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 128) return fail(MSDA_ERR_UNSUPPORTED, "device index %d", dev);
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) {
+            e = cudaGetSymbolAddress(&addr[dev], g_batched_noalloc_scratch);
+            if (e != cudaSuccess) {
+                addr[dev] = nullptr;
+                return fail(MSDA_ERR_CUDA, "msda_forward_batched_noalloc set-up: %s", cudaGetErrorString(e));
+            }
+        }
+        scratch = addr[dev];
+    }
+    return launch_forward_batched(scenes, num_scenes, total_anchors, max_ncam, Nscale, C, P, G, ft, wt, ot,
+                                  scratch, sizeof(g_batched_noalloc_scratch), done_ns, warps, blocks_per_sm,
+                                  stream);
 }
 
 }  // namespace msda

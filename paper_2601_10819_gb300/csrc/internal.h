@@ -66,6 +66,11 @@ msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int
                                    msda_dtype wt, msda_dtype ot, void* ws, size_t ws_bytes,
                                    uint64_t* done_ns, int warps, int blocks_per_sm,
                                    cudaStream_t stream);
+int batched_noalloc_max_scenes();
+msda_status launch_forward_batched_noalloc(const msda_scene* scenes, int num_scenes, int total_anchors,
+                                           int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,
+                                           msda_dtype wt, msda_dtype ot, uint64_t* done_ns, int warps,
+                                           int blocks_per_sm, cudaStream_t stream);
 msda_status launch_probe(const void* buf, size_t bytes, int reps, int blocks, int rows,
                          uint32_t* sink, cudaStream_t stream);
 
