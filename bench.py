@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--cpu-sample-anchors", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deterministic", action="store_true", help="time the deterministic backward instead")
+    ap.add_argument("--no-tune", action="store_true", help="use the built-in launch mappings")
+    ap.add_argument("--with-batched", action="store_true",
+                    help="also time the 16-scene batched serving workload (per-scene p50/p99)")
     return ap.parse_args()
 
 
@@ -181,6 +184,41 @@ def cpu_baseline(pr, sample_anchors):
                       f"fwd {t1 - t0:.2f} s + bwd {t2 - t1:.2f} s, scaled by {A}/{na}"}
 
 
+def batched_serving(dev, stream, tune_it=True, reps=20):
+    """16 uneven scenes in one persistent launch replayed from a CUDA graph: per-scene latency."""
+    from paper_2601_10819_gb300 import inputs, msda, tune
+    scenes = [s.to(dev) for s in inputs.make_workload(4, with_grad=False)]
+    cfg = tune.tune_batched(scenes) if tune_it else dict(vec=0, warps=0, bps=0)
+    plan = msda.plan_batched(scenes, warps=cfg["warps"] or None, blocks_per_sm=cfg["bps"] or None, vec=cfg["vec"])
+    plan.run()
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    lat, total = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t = plan.done_ns.cpu().double()
+        lat.extend(((t[1:] - t[0]) / 1e3).tolist())
+        total.append(e0.elapsed_time(e1) * 1e3)
+    lat.sort()
+    nominal = sum(int(np.prod(sc.weights.shape[:5])) for sc in scenes)
+    return {"scenes": len(scenes), "cameras": sum(sc.spatial_shape.shape[0] for sc in scenes),
+            "anchors": plan.total, "tuning": cfg,
+            "us_per_batch_median": statistics.median(total),
+            "scene_latency_us_p50": lat[len(lat) // 2], "scene_latency_us_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "gsamples_per_s": nominal / (statistics.median(total) * 1e-6) / 1e9}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle, timed on the host cores."""
     if rank != 0:
@@ -231,7 +269,7 @@ def main():
         return run_reference(args, rank, world)
 
     from paper_2601_10819_gb300 import build as msda_build
-    from paper_2601_10819_gb300 import inputs, msda, roofline
+    from paper_2601_10819_gb300 import inputs, msda, roofline, tune
 
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA GPU")
@@ -259,12 +297,20 @@ def main():
     if need:
         ws = torch.empty(need, dtype=torch.uint8, device=dev)
     tensors = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    fws = torch.empty(msda.forward_workspace_size(B, sum_hw, C, K, S, A, P, G), dtype=torch.uint8, device=dev)
+    if args.no_tune:
+        ft, bt = dict(vec=0, warps=0, workspace=False), dict(vec=0, warps=0)
+    else:  # autotuned launch mappings (cached per GPU model and shape); untimed
+        ft = tune.tune_forward(tensors, out, workspace=fws)
+        bt = tune.tune_backward(tensors, d.grad_out, (gf, gl, gw), deterministic=det, workspace=ws)
+    fwd_ws = fws if ft["workspace"] else None
 
     def fwd():
-        msda.forward(*tensors, out=out)
+        msda.forward(*tensors, out=out, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
 
     def bwd():
-        msda.backward(*tensors, d.grad_out, deterministic=det, workspace=ws, grads=(gf, gl, gw))
+        msda.backward(*tensors, d.grad_out, deterministic=det, workspace=ws, grads=(gf, gl, gw),
+                      warps=bt["warps"] or None, vec=bt["vec"])
 
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -328,8 +374,9 @@ def main():
         for h, dd in zip(h_in, d_in):
             dd.copy_(h, non_blocking=True)
         tens = (d_in[0], d.spatial_shape, d.scale_start_index, d_in[1], d_in[2])
-        msda.forward(*tens, out=out)
-        msda.backward(*tens, d_in[3], deterministic=det, workspace=ws, grads=(gf, gl, gw))
+        msda.forward(*tens, out=out, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
+        msda.backward(*tens, d_in[3], deterministic=det, workspace=ws, grads=(gf, gl, gw),
+                      warps=bt["warps"] or None, vec=bt["vec"])
         for h, dd in zip(h_out, (out, gf, gl, gw)):
             h.copy_(dd, non_blocking=True)
 
@@ -384,10 +431,13 @@ def main():
                     "t_us": bwd_ms * 1e3, "frac": max(t_hbm_bwd, t_l2_bwd) / (bwd_ms * 1e3)}},
         "counts": cnt.as_dict(),
         "e2e": {"value": e2e_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": (2 if not det else 4 + 3 * 3) * args.steps,
+        "gpu_launches": ((2 if fwd_ws is not None else 1) + (1 if not det else 9)) * args.steps,
+        "tuning": {"forward": ft, "backward": bt},
         "clocks": clk.summary(),
         "gpu": torch.cuda.get_device_name(dev),
     }
+    if args.with_batched:
+        line["batched_serving"] = batched_serving(dev, stream, tune_it=not args.no_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, args.cpu_sample_anchors)
     if rank == 0:

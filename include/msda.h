@@ -81,7 +81,14 @@ typedef enum { MSDA_F32 = 0, MSDA_BF16 = 1, MSDA_F16 = 2 } msda_dtype;
 typedef struct {
     int warps_per_block;   /* 1..8: warps per block (teams of lanes per block)   */
     int blocks_per_sm;     /* persistent batched kernel: resident blocks per SM  */
-    int reserved[6];
+    int variant;           /* 0 = default; 1 = msda_forward: anchor-per-block
+                              kernel even with a workspace; msda_backward
+                              (deterministic): global radix-sort form        */
+    int vectors_per_lane;  /* 16-byte feature vectors per lane and corner row
+                              (1, 2 or 4): more work per lane, fewer lanes
+                              per point; 0 = built-in default (forward 2,
+                              backward 1), else the smallest valid split     */
+    int reserved[4];
 } msda_tuning;
 
 /* ------------------------------------------------------------------------
@@ -92,14 +99,26 @@ typedef struct {
  *   B, sum_hw, Ncam, Nscale, A, P >= 0 (zero-size problems are no-ops,
  *   except that out is still written when B*A > 0); C, G >= 1; C % G == 0;
  *   Nscale <= 16.
- * Deterministic: the same inputs give bitwise-identical outputs.
+ *   workspace: NULL, or device memory of at least
+ *     msda_forward_workspace_size(...) bytes (16-byte aligned).  With a
+ *     workspace (and Nscale <= 4, (C/G)*sizeof(feat) in {16, 32, 64, 128})
+ *     the staged camera-group kernels run: each (camera, group) stages its
+ *     coarse maps in shared memory with TMA and writes per-camera partial
+ *     sums, which are then added in camera order.  Without one, one block
+ *     per anchor gathers every corner from L2/HBM.
+ * Deterministic: the same inputs and launch choice give bitwise-identical
+ * outputs (the two kernels differ in the last bits: different sum order).
  * ------------------------------------------------------------------------ */
+size_t msda_forward_workspace_size(int B, int sum_hw, int C, int Ncam, int Nscale,
+                                   int A, int P, int G);
+
 msda_status msda_forward(const void* feat, msda_dtype feat_dtype,
                          const int32_t* spatial_shape, const int32_t* scale_start_index,
                          const float* sampling_location,
                          const void* weights, msda_dtype weights_dtype,
                          void* out, msda_dtype out_dtype,
                          int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,
+                         void* workspace, size_t workspace_bytes,
                          const msda_tuning* tuning, msda_stream_t stream);
 
 /* ------------------------------------------------------------------------
@@ -119,12 +138,19 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype,
  *
  *   deterministic = 0: the feature gradient is scattered with FP32 vector
  *     atomics (summation order varies run to run, values agree to rounding).
- *   deterministic = 1: contributions are sorted by feature row with a stable
- *     radix sort and each row is reduced in a fixed order (bitwise
- *     reproducible).
+ *   deterministic = 1: no atomics; bitwise reproducible.  When the staged
+ *     kernels apply (Nscale <= 4, C/G a power of two in 4..128, at most
+ *     40960 bilinear cells per map, maps that do not overlap, A*(C/G)*4
+ *     bytes of grad_out per group fitting in shared memory): dw and dloc
+ *     come from the camera-group gather, and the feature gradient from a
+ *     stable per-map sort of the points by bilinear cell followed by one
+ *     fixed-order gather per feature row.  Otherwise (or with
+ *     tuning->variant = 1) the corner contributions are sorted by feature
+ *     row with a global stable radix sort and reduced per row.
+ *     Overlapping maps raise MSDA_ERR_OUT_OF_RANGE in the status word.
  * grad_loc and grad_weights are computed without atomics in both modes.
  * workspace: device memory of at least msda_backward_workspace_size(...)
- * bytes, 256-byte aligned (may be NULL when that size is 0).
+ * bytes, 16-byte aligned (may be NULL when that size is 0).
  * ------------------------------------------------------------------------ */
 size_t msda_backward_workspace_size(int B, int sum_hw, int C, int Ncam, int Nscale,
                                     int A, int P, int G, int deterministic);

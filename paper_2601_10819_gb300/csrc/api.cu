@@ -72,6 +72,29 @@ int dtype_size(msda_dtype t) {
     return 0;
 }
 
+static bool split_ok(int C, int G, msda_dtype t, int n, int* rt) {
+    const int sz = dtype_size(t);
+    if (sz == 0 || G <= 0 || C <= 0 || C % G || (n != 1 && n != 2 && n != 4)) return false;
+    const int cpl = (16 / sz) * n;
+    const int cg = C / G;
+    if (C % cpl || cg % cpl) return false;
+    const int r = C / cpl;
+    if (r > 32 || (r & (r - 1))) return false;
+    *rt = r;
+    return true;
+}
+
+// Prefer `want` 16-byte vectors per lane (the tuning's, else `dflt`) when
+// that split is valid; otherwise keep the smallest valid one.
+static void prefer_split(const msda_tuning* t, Problem* p, int dflt) {
+    const int want = (t && t->vectors_per_lane > 0) ? t->vectors_per_lane : dflt;
+    int rt;
+    if (want > 0 && split_ok(p->C, p->G, p->feat_t, want, &rt)) {
+        p->nv = want;
+        p->rt = rt;
+    }
+}
+
 bool pick_split(int C, int G, msda_dtype t, int* nv, int* rt) {
     const int sz = dtype_size(t);
     if (sz == 0 || G <= 0 || C <= 0 || C % G) return false;
@@ -89,11 +112,21 @@ bool pick_split(int C, int G, msda_dtype t, int* nv, int* rt) {
     return false;
 }
 
+bool pick_split_pref(int C, int G, msda_dtype t, int pref, int* nv, int* rt) {
+    if (!pick_split(C, G, t, nv, rt)) return false;
+    int r;
+    if (pref > 0 && split_ok(C, G, t, pref, &r)) {
+        *nv = pref;
+        *rt = r;
+    }
+    return true;
+}
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 static int pick_warps(const msda_tuning* t, int dflt) {
     const int w = (t && t->warps_per_block > 0) ? t->warps_per_block : dflt;
-    return w > 8 ? 8 : w;
+    return w > 8 ? 8 : w;  // the kernels are built for at most 256 threads per block
 }
 
 // Shared validation of the single-scene entry points.
@@ -138,10 +171,18 @@ const char* msda_last_error(void) { return t_err; }
 
 const char* msda_version(void) { return "msda_gb300 1.0 (sm_103a)"; }
 
+size_t msda_forward_workspace_size(int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G) {
+    if (B < 0 || sum_hw < 0 || C < 1 || Ncam < 0 || Nscale < 0 || A < 0 || P < 0 || G < 1) return 0;
+    Problem p;
+    p.B = B; p.sum_hw = sum_hw; p.C = C; p.Ncam = Ncam; p.Nscale = Nscale; p.A = A; p.P = P; p.G = G;
+    return cg_forward_workspace(p);
+}
+
 msda_status msda_forward(const void* feat, msda_dtype feat_dtype, const int32_t* spatial_shape,
                          const int32_t* scale_start_index, const float* sampling_location,
                          const void* weights, msda_dtype weights_dtype, void* out, msda_dtype out_dtype,
                          int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,
+                         void* workspace, size_t workspace_bytes,
                          const msda_tuning* tuning, msda_stream_t stream) {
     t_err[0] = 0;
     Problem p;
@@ -151,6 +192,12 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype, const int32_t*
     if (dtype_size(out_dtype) == 0) return fail(MSDA_ERR_INVALID_ARG, "msda_forward: unknown out dtype");
     if ((long long)B * A > 0 && !out) return fail(MSDA_ERR_INVALID_ARG, "msda_forward: out is NULL");
     if (!aligned16(out)) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: out must be 16-byte aligned");
+    prefer_split(tuning, &p, 2);
+    const bool direct = tuning && tuning->variant == 1;  // force the anchor-per-block kernel
+    if (workspace && !direct && cg_supported(p)) {
+        if (!aligned16(workspace)) return fail(MSDA_ERR_WORKSPACE, "msda_forward: workspace must be 16-byte aligned");
+        return launch_forward_cg(p, out, out_dtype, workspace, workspace_bytes, (cudaStream_t)stream);
+    }
     return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream);
 }
 
@@ -160,7 +207,9 @@ size_t msda_backward_workspace_size(int B, int sum_hw, int C, int Ncam, int Nsca
         return 0;
     Problem p;
     p.B = B; p.sum_hw = sum_hw; p.C = C; p.Ncam = Ncam; p.Nscale = Nscale; p.A = A; p.P = P; p.G = G;
-    return backward_det_workspace(p);
+    p.Cg = C / G;
+    const size_t a = backward_det_workspace(p), b = cg_backward_workspace(p);
+    return a > b ? a : b;
 }
 
 msda_status msda_backward(const void* feat, msda_dtype feat_dtype, const int32_t* spatial_shape,
@@ -183,10 +232,15 @@ msda_status msda_backward(const void* feat, msda_dtype feat_dtype, const int32_t
     if (!aligned16(grad_out) || !aligned16(grad_feat) || !aligned16(grad_loc) || !aligned16(grad_weights))
         return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: gradient pointers must be 16-byte aligned");
     if (p.C % 4 != 0) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: C must be a multiple of 4");
-    const int warps = pick_warps(tuning, 8);
+    prefer_split(tuning, &p, 0);
+    const int warps = pick_warps(tuning, 4);
     if (deterministic) {
         if (workspace && !aligned16(workspace))
             return fail(MSDA_ERR_WORKSPACE, "msda_backward: workspace must be 256-byte aligned");
+        const bool sorted_rows = tuning && tuning->variant == 1;  // force the radix-sort form
+        if (!sorted_rows && cg_supported(p))
+            return launch_backward_cg(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes,
+                                      (cudaStream_t)stream);
         return launch_backward_det(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes,
                                    warps, (cudaStream_t)stream);
     }
@@ -219,6 +273,7 @@ msda_status msda_forward_batched(const msda_scene* scenes, int num_scenes, int t
     return launch_forward_batched(scenes, num_scenes, total_anchors, max_ncam, Nscale, C, P, G, feat_dtype,
                                   weights_dtype, out_dtype, workspace, workspace_bytes, scene_done_ns,
                                   pick_warps(tuning, 8), tuning ? tuning->blocks_per_sm : 0,
+                                  tuning && tuning->vectors_per_lane > 0 ? tuning->vectors_per_lane : 2,
                                   (cudaStream_t)stream);
 }
 
@@ -247,7 +302,9 @@ msda_status msda_forward_batched_noalloc(const msda_scene* scenes, int num_scene
         return fail(MSDA_ERR_UNSUPPORTED, "%s: pointers must be 16-byte aligned", fn);
     return launch_forward_batched_noalloc(scenes, num_scenes, total_anchors, max_ncam, Nscale, C, P, G, feat_dtype,
                                           weights_dtype, out_dtype, scene_done_ns, pick_warps(tuning, 8),
-                                          tuning ? tuning->blocks_per_sm : 0, (cudaStream_t)stream);
+                                          tuning ? tuning->blocks_per_sm : 0,
+                                          tuning && tuning->vectors_per_lane > 0 ? tuning->vectors_per_lane : 2,
+                                          (cudaStream_t)stream);
 }
 
 msda_status msda_get_device_status(msda_stream_t stream) {

@@ -51,14 +51,17 @@ __device__ __forceinline__ float team_sum(float v, unsigned mask, int width) {
 }
 
 template <typename FT, typename WT, int NV>
-__global__ void __launch_bounds__(256, NV == 1 ? 4 : 2) bwd_atomic_kernel(const BwdArgs p) {
+__global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
     constexpr int VEC = Elem<FT>::VEC;
     constexpr int CPL = VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nmaps = p.Ncam * p.Nscale;
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem);
+    float4* sbox = reinterpret_cast<float4*>(smem + align16(sizeof(MapInfo) * (size_t)nmaps));
     for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
         smap[i] = load_map(p.shape, p.start, i, p.sum_hw, p.status);
+    __syncthreads();
+    for (int k = threadIdx.x; k < p.Ncam; k += blockDim.x) sbox[k] = camera_box(smap + k * p.Nscale, p.Nscale);
     __syncthreads();
 
     const int tpw = 32 / p.rt;
@@ -87,18 +90,26 @@ __global__ void __launch_bounds__(256, NV == 1 ? 4 : 2) bwd_atomic_kernel(const 
         const int b = (int)(ba / p.A);
         const long long pk = (ba * p.P + pp) * p.Ncam + k;
         const float2 uv = __ldg(reinterpret_cast<const float2*>(p.loc) + pk);
+        float* gwrow = p.gw + pk * p.Nscale * p.G + g;
+        if (!in_box(uv, sbox[k])) {
+            // dropped at every scale: zero gradients for the point
+            if ((tl & (lg - 1)) == 0)
+                for (int s = 0; s < p.Nscale; ++s) gwrow[(long long)s * p.G] = 0.0f;
+            if (tl == 0) reinterpret_cast<float2*>(p.gloc)[pk] = make_float2(0.0f, 0.0f);
+            continue;
+        }
         const float* gorow = p.go + ba * p.C;
-        float go[CPL];
+        float2 go[CPL / 2];
 #pragma unroll
         for (int j = 0; j < CPL / 4; ++j) {
             const float4 t = __ldg(reinterpret_cast<const float4*>(gorow + c0) + j);
-            go[4 * j + 0] = t.x; go[4 * j + 1] = t.y; go[4 * j + 2] = t.z; go[4 * j + 3] = t.w;
+            go[2 * j] = make_float2(t.x, t.y);
+            go[2 * j + 1] = make_float2(t.z, t.w);
         }
         const FT* fb = reinterpret_cast<const FT*>(p.feat) + (long long)b * p.sum_hw * p.C + c0;
         float* gfb = p.gfeat + (long long)b * p.sum_hw * p.C + ci;
         const WT* wpt = reinterpret_cast<const WT*>(p.w) + pk * p.Nscale * p.G;  // weights of this point
         const WT* wrow = wpt + g;
-        float* gwrow = p.gw + pk * p.Nscale * p.G + g;
         const MapInfo* mrow = smap + k * p.Nscale;
         float du = 0.0f, dv = 0.0f;
         for (int s = 0; s < p.Nscale; ++s) {
@@ -107,57 +118,67 @@ __global__ void __launch_bounds__(256, NV == 1 ? 4 : 2) bwd_atomic_kernel(const 
             const bool in = (m.W != 0) && locate(uv.x, uv.y, m.H, m.W, c);  // uniform over the team
             float dwp = 0.0f;
             if (in) {
-                const float wv = ldw(wrow + (long long)s * p.G);
+                const float wvs = ldw(wrow + (long long)s * p.G);
                 const bool vx0 = c.x0 >= 0, vx1 = c.x0 + 1 < m.W;
                 const bool vy0 = c.y0 >= 0, vy1 = c.y0 + 1 < m.H;
-                const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
-                const float o00 = ax * ay, o01 = c.fx * ay, o10 = ax * c.fy, o11 = c.fx * c.fy;
                 const long long r00 = (long long)(m.start + c.y0 * m.W + c.x0) * p.C;
                 const long long rW = (long long)m.W * p.C;
                 const FT* p00 = fb + r00;
-                uint4 q00[NV], q01[NV], q10[NV], q11[NV];
-                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                uint4 q[4][NV];
+                if (vx0 && vx1 && vy0 && vy1) {
 #pragma unroll
-                for (int n = 0; n < NV; ++n) {
-                    q00[n] = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
-                    q01[n] = (vy0 && vx1) ? ld16(p00 + p.C + n * VEC) : z;
-                    q10[n] = (vy1 && vx0) ? ld16(p00 + rW + n * VEC) : z;
-                    q11[n] = (vy1 && vx1) ? ld16(p00 + rW + p.C + n * VEC) : z;
-                }
-                float gxp = 0.0f, gyp = 0.0f;
+                    for (int n = 0; n < NV; ++n) {
+                        q[0][n] = ld16(p00 + n * VEC);
+                        q[1][n] = ld16(p00 + p.C + n * VEC);
+                        q[2][n] = ld16(p00 + rW + n * VEC);
+                        q[3][n] = ld16(p00 + rW + p.C + n * VEC);
+                    }
+                } else {
+                    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                for (int n = 0; n < NV; ++n) {
-                    float f00[VEC], f01[VEC], f10[VEC], f11[VEC];
-                    widen(q00[n], f00, FT());
-                    widen(q01[n], f01, FT());
-                    widen(q10[n], f10, FT());
-                    widen(q11[n], f11, FT());
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) {
-                        const float gj = go[n * VEC + j];
-                        const float S = o00 * f00[j] + o01 * f01[j] + o10 * f10[j] + o11 * f11[j];
-                        dwp = fmaf(gj, S, dwp);
-                        gxp = fmaf(gj, ay * (f01[j] - f00[j]) + c.fy * (f11[j] - f10[j]), gxp);
-                        gyp = fmaf(gj, ax * (f10[j] - f00[j]) + c.fx * (f11[j] - f01[j]), gyp);
+                    for (int n = 0; n < NV; ++n) {
+                        q[0][n] = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
+                        q[1][n] = (vy0 && vx1) ? ld16(p00 + p.C + n * VEC) : z;
+                        q[2][n] = (vy1 && vx0) ? ld16(p00 + rW + n * VEC) : z;
+                        q[3][n] = (vy1 && vx1) ? ld16(p00 + rW + p.C + n * VEC) : z;
                     }
                 }
-                du = fmaf((float)m.W * wv, gxp, du);
-                dv = fmaf((float)m.H * wv, gyp, dv);
+                // d[q] = sum over this lane's channels of go * F_q (packed pairs)
+                float2 d2[4];
+#pragma unroll
+                for (int cq = 0; cq < 4; ++cq) d2[cq] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+#pragma unroll
+                    for (int cq = 0; cq < 4; ++cq) {
+                        float2 f[VEC / 2];
+                        widen2(q[cq][n], f, FT());
+#pragma unroll
+                        for (int j = 0; j < VEC / 2; ++j) d2[cq] = __ffma2_rn(go[n * (VEC / 2) + j], f[j], d2[cq]);
+                    }
+                }
+                const float d00 = d2[0].x + d2[0].y, d01 = d2[1].x + d2[1].y;
+                const float d10 = d2[2].x + d2[2].y, d11 = d2[3].x + d2[3].y;
+                const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
+                const float o00 = ax * ay, o01 = c.fx * ay, o10 = ax * c.fy, o11 = c.fx * c.fy;
+                dwp = o00 * d00 + o01 * d01 + o10 * d10 + o11 * d11;
+                du = fmaf((float)m.W * wvs, ay * (d01 - d00) + c.fy * (d11 - d10), du);
+                dv = fmaf((float)m.H * wvs, ax * (d10 - d00) + c.fx * (d11 - d01), dv);
                 if (p.scatter) {
                     // feature gradient w * omega * go, in the interleaved layout: each warp-wide
-                    // 16-byte vector atomic covers 4*rt contiguous channels (whole sectors)
-                    // (an interleaved chunk belongs to its own group, with its own weight)
+                    // 16-byte vector atomic covers 4*rt contiguous channels (whole sectors);
+                    // an interleaved chunk belongs to its own group, with its own weight
                     float* g00 = gfb + r00;
 #pragma unroll
                     for (int j = 0; j < CPL / 4; ++j) {
                         const float wj = ldw(wpt + (long long)s * p.G + (ci + j * cstride) / p.Cg);
                         const float c00 = wj * o00, c01 = wj * o01, c10 = wj * o10, c11 = wj * o11;
                         const float4 gv = __ldg(reinterpret_cast<const float4*>(gorow + ci + j * cstride));
-                        float* q = g00 + j * cstride;
-                        if (vy0 && vx0) atomicAdd(reinterpret_cast<float4*>(q), scale4(c00, gv));
-                        if (vy0 && vx1) atomicAdd(reinterpret_cast<float4*>(q + p.C), scale4(c01, gv));
-                        if (vy1 && vx0) atomicAdd(reinterpret_cast<float4*>(q + rW), scale4(c10, gv));
-                        if (vy1 && vx1) atomicAdd(reinterpret_cast<float4*>(q + rW + p.C), scale4(c11, gv));
+                        float* qq = g00 + j * cstride;
+                        if (vy0 && vx0) atomicAdd(reinterpret_cast<float4*>(qq), scale4(c00, gv));
+                        if (vy0 && vx1) atomicAdd(reinterpret_cast<float4*>(qq + p.C), scale4(c01, gv));
+                        if (vy1 && vx0) atomicAdd(reinterpret_cast<float4*>(qq + rW), scale4(c10, gv));
+                        if (vy1 && vx1) atomicAdd(reinterpret_cast<float4*>(qq + rW + p.C), scale4(c11, gv));
                     }
                 }
             }
@@ -192,7 +213,9 @@ static BwdKernel bwd_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
     return nullptr;
 }
 
-size_t bwd_smem_bytes(const Problem& p) { return sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale; }
+size_t bwd_smem_bytes(const Problem& p) {
+    return align16(sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale) + sizeof(float4) * (size_t)p.Ncam;
+}
 
 msda_status launch_backward_atomic(const Problem& p, const float* grad_out, float* grad_feat,
                                    float* grad_loc, float* grad_w, int warps, cudaStream_t stream) {

@@ -62,6 +62,22 @@ __device__ __forceinline__ void widen(const uint4& v, float* f, __half) {
     }
 }
 
+// Widen 16 bytes into VEC/2 channel pairs (for packed FP32 math).
+__device__ __forceinline__ void widen2(const uint4& v, float2* f, float) {
+    f[0] = make_float2(__uint_as_float(v.x), __uint_as_float(v.y));
+    f[1] = make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
+}
+__device__ __forceinline__ void widen2(const uint4& v, float2* f, __nv_bfloat16) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f[i] = make_float2(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xffff0000u));
+}
+__device__ __forceinline__ void widen2(const uint4& v, float2* f, __half) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f[i] = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+}
+
 // Scalar weight load widened to FP32.
 __device__ __forceinline__ float ldw(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldw(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
@@ -147,6 +163,28 @@ __device__ __forceinline__ MapInfo load_map(const int32_t* shape, const int32_t*
         m.start = 0;
     }
     return m;
+}
+
+// Normalised box outside of which a point is dropped at every scale of a
+// camera: a point is kept at scale s iff u in (-0.5/W_s, 1 + 0.5/W_s) and
+// v in (-0.5/H_s, 1 + 0.5/H_s), so the union over scales is the box of the
+// smallest W and H.  The box is widened by a relative 1e-3 so rounding can
+// only keep extra points (each scale still runs the exact test).
+// Returns (u_lo, u_hi, v_lo, v_hi); an empty box if no map is valid.
+__device__ __forceinline__ float4 camera_box(const MapInfo* maps, int Nscale) {
+    int wmin = 0, hmin = 0;
+    for (int s = 0; s < Nscale; ++s) {
+        if (maps[s].W == 0) continue;
+        if (wmin == 0 || maps[s].W < wmin) wmin = maps[s].W;
+        if (hmin == 0 || maps[s].H < hmin) hmin = maps[s].H;
+    }
+    if (wmin == 0) return make_float4(1.0f, 0.0f, 1.0f, 0.0f);
+    const float mu = 0.5f / (float)wmin * 1.001f + 1e-6f, mv = 0.5f / (float)hmin * 1.001f + 1e-6f;
+    return make_float4(-mu, 1.0f + mu, -mv, 1.0f + mv);
+}
+
+__device__ __forceinline__ bool in_box(float2 uv, float4 b) {
+    return uv.x > b.x && uv.x < b.y && uv.y > b.z && uv.y < b.w;  // false for NaN
 }
 
 }  // namespace msda

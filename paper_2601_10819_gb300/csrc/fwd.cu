@@ -44,77 +44,83 @@ struct FwdArgs {
 
 // Shared-memory carve-up of a forward block.
 struct FwdSmem {
-    size_t maps, loc, part, total;
+    size_t maps, box, loc, part, total;
     __host__ __device__ FwdSmem(int nmaps, int P, int Ncam, int nteams, int C) {
         maps = 0;
-        loc = align_up_dev(sizeof(MapInfo) * (size_t)nmaps, 16);
-        part = loc + align_up_dev(sizeof(float2) * (size_t)P * Ncam, 16);
+        box = align16(sizeof(MapInfo) * (size_t)nmaps);
+        loc = box + sizeof(float4) * (size_t)Ncam;
+        part = loc + align16(sizeof(float2) * (size_t)P * Ncam);
         total = part + sizeof(float) * (size_t)nteams * C;
     }
-    __host__ __device__ static size_t align_up_dev(size_t x, size_t a) { return (x + a - 1) / a * a; }
 };
 
 // Accumulate the items of one anchor dealt to this team.
 //   fb: feat of batch element b, offset to the lane's first channel
 //   wb: weights of the anchor, offset to the lane's group
+// Items outside the camera's box are skipped with one test.  Per scale, the
+// four corner rows are loaded (NV 16-byte chunks each; unpredicated when the
+// cell is inside the map) and accumulated with packed FP32 FMAs.
 template <typename FT, typename WT, int NV>
 __device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, const WT* __restrict__ wb,
-                                                  const MapInfo* __restrict__ smap,
+                                                  const MapInfo* __restrict__ smap, const float4* __restrict__ sbox,
                                                   const float2* __restrict__ sloc, int C, int Ncam,
                                                   int Nscale, int P, int G, int team, int nteams,
-                                                  float* acc) {
+                                                  float2* acc) {
     constexpr int VEC = Elem<FT>::VEC;
     const int nitems = Ncam * P;
     for (int item = team; item < nitems; item += nteams) {
         const int k = item / P;
         const int pp = item - k * P;
         const float2 uv = sloc[pp * Ncam + k];
+        if (!in_box(uv, sbox[k])) continue;
         const WT* wrow = wb + ((long long)pp * Ncam + k) * Nscale * G;
         const MapInfo* mrow = smap + k * Nscale;
-        for (int s0 = 0; s0 < Nscale; s0 += kScaleChunk) {
+        for (int s = 0; s < Nscale; ++s) {
+            const MapInfo m = mrow[s];
+            Cell c;
+            if (m.W == 0 || !locate(uv.x, uv.y, m.H, m.W, c)) continue;
+            const float wv = ldw(wrow + (long long)s * G);
+            const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
+            const float2 w00 = make_float2(wv * (ax * ay), wv * (ax * ay));
+            const float2 w01 = make_float2(wv * (c.fx * ay), wv * (c.fx * ay));
+            const float2 w10 = make_float2(wv * (ax * c.fy), wv * (ax * c.fy));
+            const float2 w11 = make_float2(wv * (c.fx * c.fy), wv * (c.fx * c.fy));
+            const FT* p00 = fb + (long long)(m.start + c.y0 * m.W + c.x0) * C;
+            const FT* p10 = p00 + (long long)m.W * C;
+            uint4 q[4][NV];
+            if (c.x0 >= 0 && c.x0 + 1 < m.W && c.y0 >= 0 && c.y0 + 1 < m.H) {
 #pragma unroll
-            for (int ds = 0; ds < kScaleChunk; ++ds) {
-                const int s = s0 + ds;
-                if (s >= Nscale) break;
-                const MapInfo m = mrow[s];
-                Cell c;
-                if (m.W == 0 || !locate(uv.x, uv.y, m.H, m.W, c)) continue;
-                const float wv = ldw(wrow + (long long)s * G);
+                for (int n = 0; n < NV; ++n) {
+                    q[0][n] = ld16(p00 + n * VEC);
+                    q[1][n] = ld16(p00 + C + n * VEC);
+                    q[2][n] = ld16(p10 + n * VEC);
+                    q[3][n] = ld16(p10 + C + n * VEC);
+                }
+            } else {
                 const bool vx0 = c.x0 >= 0, vx1 = c.x0 + 1 < m.W;
                 const bool vy0 = c.y0 >= 0, vy1 = c.y0 + 1 < m.H;
-                const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
-                const float w00 = wv * (ax * ay), w01 = wv * (c.fx * ay);
-                const float w10 = wv * (ax * c.fy), w11 = wv * (c.fx * c.fy);
-                const long long r00 = (long long)(m.start + c.y0 * m.W + c.x0) * C;
-                const FT* p00 = fb + r00;
-                const FT* p01 = p00 + C;
-                const FT* p10 = p00 + (long long)m.W * C;
-                const FT* p11 = p10 + C;
-                uint4 q00[NV], q01[NV], q10[NV], q11[NV];
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
                 for (int n = 0; n < NV; ++n) {
-                    q00[n] = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
-                    q01[n] = (vy0 && vx1) ? ld16(p01 + n * VEC) : z;
-                    q10[n] = (vy1 && vx0) ? ld16(p10 + n * VEC) : z;
-                    q11[n] = (vy1 && vx1) ? ld16(p11 + n * VEC) : z;
+                    q[0][n] = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
+                    q[1][n] = (vy0 && vx1) ? ld16(p00 + C + n * VEC) : z;
+                    q[2][n] = (vy1 && vx0) ? ld16(p10 + n * VEC) : z;
+                    q[3][n] = (vy1 && vx1) ? ld16(p10 + C + n * VEC) : z;
                 }
+            }
 #pragma unroll
-                for (int n = 0; n < NV; ++n) {
-                    float f00[VEC], f01[VEC], f10[VEC], f11[VEC];
-                    widen(q00[n], f00, FT());
-                    widen(q01[n], f01, FT());
-                    widen(q10[n], f10, FT());
-                    widen(q11[n], f11, FT());
+            for (int n = 0; n < NV; ++n) {
+                float2 f[4][VEC / 2];
 #pragma unroll
-                    for (int j = 0; j < VEC; ++j) {
-                        float a = acc[n * VEC + j];
-                        a = fmaf(w00, f00[j], a);
-                        a = fmaf(w01, f01[j], a);
-                        a = fmaf(w10, f10[j], a);
-                        a = fmaf(w11, f11[j], a);
-                        acc[n * VEC + j] = a;
-                    }
+                for (int cq = 0; cq < 4; ++cq) widen2(q[cq][n], f[cq], FT());
+#pragma unroll
+                for (int j = 0; j < VEC / 2; ++j) {
+                    float2 a = acc[n * (VEC / 2) + j];
+                    a = __ffma2_rn(w00, f[0][j], a);
+                    a = __ffma2_rn(w01, f[1][j], a);
+                    a = __ffma2_rn(w10, f[2][j], a);
+                    a = __ffma2_rn(w11, f[3][j], a);
+                    acc[n * (VEC / 2) + j] = a;
                 }
             }
         }
@@ -137,8 +143,12 @@ __device__ __forceinline__ void reduce_and_store(const float* spart, int nteams,
     }
 }
 
+// One block per anchor.  The launch is sized so that, on the benchmark
+// shapes, every anchor's block is resident at once: then all blocks walk the
+// cameras in the same order together and each camera's maps are read from
+// HBM about once.
 template <typename FT, typename WT, int NV>
-__global__ void __launch_bounds__(256, NV == 1 ? 6 : 3) fwd_anchor_kernel(const FwdArgs p) {
+__global__ void __launch_bounds__(256) fwd_anchor_kernel(const FwdArgs p) {
     constexpr int CPL = Elem<FT>::VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nmaps = p.Ncam * p.Nscale;
@@ -146,6 +156,7 @@ __global__ void __launch_bounds__(256, NV == 1 ? 6 : 3) fwd_anchor_kernel(const 
     const int nteams = (blockDim.x >> 5) * tpw;
     const FwdSmem lay(nmaps, p.P, p.Ncam, nteams, p.C);
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
+    float4* sbox = reinterpret_cast<float4*>(smem + lay.box);
     float2* sloc = reinterpret_cast<float2*>(smem + lay.loc);
     float* spart = reinterpret_cast<float*>(smem + lay.part);
 
@@ -156,6 +167,8 @@ __global__ void __launch_bounds__(256, NV == 1 ? 6 : 3) fwd_anchor_kernel(const 
     const float2* gloc = reinterpret_cast<const float2*>(p.loc) + ba * (long long)(p.P * p.Ncam);
     for (int i = threadIdx.x; i < p.P * p.Ncam; i += blockDim.x) sloc[i] = __ldg(gloc + i);
     __syncthreads();
+    for (int k = threadIdx.x; k < p.Ncam; k += blockDim.x) sbox[k] = camera_box(smap + k * p.Nscale, p.Nscale);
+    __syncthreads();
 
     const int lane = threadIdx.x & 31;
     const int team = (threadIdx.x >> 5) * tpw + lane / p.rt;
@@ -164,14 +177,15 @@ __global__ void __launch_bounds__(256, NV == 1 ? 6 : 3) fwd_anchor_kernel(const 
     const FT* fb = reinterpret_cast<const FT*>(p.feat) + (long long)b * p.sum_hw * p.C + c0;
     const WT* wb = reinterpret_cast<const WT*>(p.w) + ba * ((long long)p.P * p.Ncam * p.Nscale * p.G) + g;
 
-    float acc[CPL];
+    float2 acc[CPL / 2];
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) acc[j] = 0.0f;
-    accumulate_anchor<FT, WT, NV>(fb, wb, smap, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc);
+    for (int j = 0; j < CPL / 2; ++j) acc[j] = make_float2(0.0f, 0.0f);
+    accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc);
 
     float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
-    for (int j = 0; j < CPL; j += 4) *reinterpret_cast<float4*>(mine + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    for (int j = 0; j < CPL / 2; j += 2)
+        *reinterpret_cast<float4*>(mine + 2 * j) = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
     __syncthreads();
     reduce_and_store(spart, nteams, p.C, p.out, p.out_t, ba);
 }
@@ -203,13 +217,14 @@ __device__ __forceinline__ uint64_t globaltimer() {
 }
 
 template <typename FT, typename WT, int NV>
-__global__ void __launch_bounds__(512) fwd_batched_kernel(const BatchedArgs p) {
+__global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
     constexpr int CPL = Elem<FT>::VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int tpw = 32 / p.rt;
     const int nteams = (blockDim.x >> 5) * tpw;
     const FwdSmem lay(p.max_ncam * p.Nscale, p.P, p.max_ncam, nteams, p.C);
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
+    float4* sbox = reinterpret_cast<float4*>(smem + lay.box);
     float2* sloc = reinterpret_cast<float2*>(smem + lay.loc);
     float* spart = reinterpret_cast<float*>(smem + lay.part);
     __shared__ int s_unit, s_scene;
@@ -253,15 +268,19 @@ __global__ void __launch_bounds__(512) fwd_batched_kernel(const BatchedArgs p) {
             const float2* gloc = reinterpret_cast<const float2*>(S.sampling_location) + (long long)a * (p.P * ncam);
             for (int i = threadIdx.x; i < p.P * ncam; i += blockDim.x) sloc[i] = __ldg(gloc + i);
             __syncthreads();
+            if (sc != cur_scene)
+                for (int k = threadIdx.x; k < ncam; k += blockDim.x) sbox[k] = camera_box(smap + k * p.Nscale, p.Nscale);
+            __syncthreads();
             const FT* fb = reinterpret_cast<const FT*>(S.feat) + c0;
             const WT* wb = reinterpret_cast<const WT*>(S.weights) + (long long)a * ((long long)p.P * ncam * p.Nscale * p.G) + g;
-            float acc[CPL];
+            float2 acc[CPL / 2];
 #pragma unroll
-            for (int j = 0; j < CPL; ++j) acc[j] = 0.0f;
-            accumulate_anchor<FT, WT, NV>(fb, wb, smap, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc);
+            for (int j = 0; j < CPL / 2; ++j) acc[j] = make_float2(0.0f, 0.0f);
+            accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc);
             float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
-            for (int j = 0; j < CPL; j += 4) *reinterpret_cast<float4*>(mine + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+            for (int j = 0; j < CPL / 2; j += 2)
+                *reinterpret_cast<float4*>(mine + 2 * j) = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
             __syncthreads();
             reduce_and_store(spart, nteams, p.C, S.out, p.out_t, a);
             cur_scene = sc;
@@ -348,13 +367,13 @@ size_t batched_workspace(int num_scenes) { return align_up(sizeof(unsigned int) 
 msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int total_anchors,
                                    int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,
                                    msda_dtype wt, msda_dtype ot, void* ws, size_t ws_bytes,
-                                   uint64_t* done_ns, int warps, int blocks_per_sm,
+                                   uint64_t* done_ns, int warps, int blocks_per_sm, int vec,
                                    cudaStream_t stream) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);
     if (st != MSDA_OK) return st;
     int nv, rt;
-    if (!pick_split(C, G, ft, &nv, &rt))
+    if (!pick_split_pref(C, G, ft, vec, &nv, &rt))
         return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_batched: no lane split for C=%d G=%d", C, G);
     BatchedKernel k = batched_kernel_for(ft, wt, nv);
     if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_batched: unsupported dtype pair");
@@ -406,7 +425,7 @@ int batched_noalloc_max_scenes() { return kNoAllocMaxScenes; }
 msda_status launch_forward_batched_noalloc(const msda_scene* scenes, int num_scenes, int total_anchors,
                                            int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,
                                            msda_dtype wt, msda_dtype ot, uint64_t* done_ns, int warps,
-                                           int blocks_per_sm, cudaStream_t stream) {
+                                           int blocks_per_sm, int vec, cudaStream_t stream) {
     if (num_scenes > kNoAllocMaxScenes)
         return fail(MSDA_ERR_INVALID_ARG, "msda_forward_batched_noalloc: %d scenes exceed the built-in limit of %d",
                     num_scenes, kNoAllocMaxScenes);
@@ -429,7 +448,7 @@ msda_status launch_forward_batched_noalloc(const msda_scene* scenes, int num_sce
         scratch = addr[dev];
     }
     return launch_forward_batched(scenes, num_scenes, total_anchors, max_ncam, Nscale, C, P, G, ft, wt, ot,
-                                  scratch, sizeof(g_batched_noalloc_scratch), done_ns, warps, blocks_per_sm,
+                                  scratch, sizeof(g_batched_noalloc_scratch), done_ns, warps, blocks_per_sm, vec,
                                   stream);
 }
 

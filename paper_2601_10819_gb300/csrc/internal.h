@@ -45,6 +45,8 @@ msda_status ensure_smem(const void* func, size_t bytes, const DeviceInfo& dev);
 
 // Lanes-per-row / chunks-per-lane split for C channels of `t`, or false.
 bool pick_split(int C, int G, msda_dtype t, int* nv, int* rt);
+// As pick_split, but take `pref` vectors per lane when that split is valid.
+bool pick_split_pref(int C, int G, msda_dtype t, int pref, int* nv, int* rt);
 
 int dtype_size(msda_dtype t);
 
@@ -64,13 +66,20 @@ size_t batched_workspace(int num_scenes);
 msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int total_anchors,
                                    int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,
                                    msda_dtype wt, msda_dtype ot, void* ws, size_t ws_bytes,
-                                   uint64_t* done_ns, int warps, int blocks_per_sm,
+                                   uint64_t* done_ns, int warps, int blocks_per_sm, int vec,
                                    cudaStream_t stream);
 int batched_noalloc_max_scenes();
 msda_status launch_forward_batched_noalloc(const msda_scene* scenes, int num_scenes, int total_anchors,
                                            int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,
                                            msda_dtype wt, msda_dtype ot, uint64_t* done_ns, int warps,
-                                           int blocks_per_sm, cudaStream_t stream);
+                                           int blocks_per_sm, int vec, cudaStream_t stream);
+bool cg_supported(const Problem& p);
+size_t cg_forward_workspace(const Problem& p);
+size_t cg_backward_workspace(const Problem& p);
+msda_status launch_forward_cg(const Problem& p, void* out, msda_dtype out_t, void* ws, size_t ws_bytes,
+                              cudaStream_t stream);
+msda_status launch_backward_cg(const Problem& p, const float* grad_out, float* grad_feat, float* grad_loc,
+                               float* grad_w, void* ws, size_t ws_bytes, cudaStream_t stream);
 msda_status launch_probe(const void* buf, size_t bytes, int reps, int blocks, int rows,
                          uint32_t* sink, cudaStream_t stream);
 

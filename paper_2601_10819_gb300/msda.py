@@ -40,7 +40,7 @@ class MSDAError(RuntimeError):
 
 class msda_tuning(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("variant", ctypes.c_int), ("vectors_per_lane", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class msda_scene(ctypes.Structure):
@@ -66,7 +66,9 @@ def load(path: Optional[str] = None):
         lib = ctypes.CDLL(p)
         vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
         tp = ctypes.POINTER(msda_tuning)
-        lib.msda_forward.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i] + [i] * 8 + [tp, vp]
+        lib.msda_forward_workspace_size.argtypes = [i] * 8
+        lib.msda_forward_workspace_size.restype = sz
+        lib.msda_forward.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i] + [i] * 8 + [vp, sz, tp, vp]
         lib.msda_forward.restype = i
         lib.msda_backward_workspace_size.argtypes = [i] * 9
         lib.msda_backward_workspace_size.restype = sz
@@ -98,12 +100,14 @@ def _stream(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
-def _tuning(warps: Optional[int], blocks_per_sm: Optional[int] = None):
-    if not warps and not blocks_per_sm:
+def _tuning(warps: Optional[int], blocks_per_sm: Optional[int] = None, variant: int = 0, vec: int = 0):
+    if not warps and not blocks_per_sm and not variant and not vec:
         return None
     t = msda_tuning()
     t.warps_per_block = int(warps or 0)
     t.blocks_per_sm = int(blocks_per_sm or 0)
+    t.variant = int(variant)
+    t.vectors_per_lane = int(vec or 0)
     return ctypes.byref(t)
 
 
@@ -137,19 +141,36 @@ def _dims(feat, spatial_shape, scale_start_index, sampling_location, weights):
     return B, sum_hw, C, Ncam, Nscale, A, P, G
 
 
+def forward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G) -> int:
+    return int(load().msda_forward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G))
+
+
+AUTO = "auto"
+
+
 def forward(feat, spatial_shape, scale_start_index, sampling_location, weights, *,
             out: Optional[torch.Tensor] = None, out_dtype: torch.dtype = torch.float32,
-            warps: Optional[int] = None) -> torch.Tensor:
-    """msda_forward: out[B, A, C] on the current stream of feat's device."""
+            workspace=AUTO, warps: Optional[int] = None, variant: int = 0, vec: int = 0) -> torch.Tensor:
+    """msda_forward: out[B, A, C] on the current stream of feat's device.
+
+    workspace: "auto" (a buffer from torch's allocator, which enables the
+    staged camera-group kernels), a uint8 CUDA tensor, or None (the
+    anchor-per-block kernel, no scratch).
+    """
     lib = load()
     B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
     if out is None:
         out = torch.empty(B, A, C, dtype=out_dtype, device=feat.device)
     elif out.shape != (B, A, C) or not out.is_contiguous() or out.dtype not in _DT:
         raise ValueError("out must be a contiguous [B, A, C] tensor")
+    if isinstance(workspace, str):
+        need = forward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G)
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=feat.device)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     rc = lib.msda_forward(_ptr(feat), _DT[feat.dtype], _ptr(spatial_shape), _ptr(scale_start_index),
                           _ptr(sampling_location), _ptr(weights), _DT[weights.dtype], _ptr(out), _DT[out.dtype],
-                          B, sum_hw, C, Ncam, Nscale, A, P, G, _tuning(warps), ctypes.c_void_p(_stream(feat.device)))
+                          B, sum_hw, C, Ncam, Nscale, A, P, G, _ptr(workspace), ws_bytes, _tuning(warps, None, variant, vec),
+                          ctypes.c_void_p(_stream(feat.device)))
     _check("msda_forward", rc)
     return out
 
@@ -160,7 +181,7 @@ def backward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G, deterministic: 
 
 def backward(feat, spatial_shape, scale_start_index, sampling_location, weights, grad_out, *,
              deterministic: bool = False, workspace: Optional[torch.Tensor] = None,
-             grads=None, warps: Optional[int] = None):
+             grads=None, warps: Optional[int] = None, variant: int = 0, vec: int = 0):
     """msda_backward: (grad_feat, grad_loc, grad_weights), all float32."""
     lib = load()
     B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
@@ -180,7 +201,7 @@ def backward(feat, spatial_shape, scale_start_index, sampling_location, weights,
     rc = lib.msda_backward(_ptr(feat), _DT[feat.dtype], _ptr(spatial_shape), _ptr(scale_start_index),
                            _ptr(sampling_location), _ptr(weights), _DT[weights.dtype], _ptr(grad_out),
                            _ptr(gf), _ptr(gl), _ptr(gw), B, sum_hw, C, Ncam, Nscale, A, P, G,
-                           int(bool(deterministic)), _ptr(workspace), ws_bytes, _tuning(warps),
+                           int(bool(deterministic)), _ptr(workspace), ws_bytes, _tuning(warps, None, variant, vec),
                            ctypes.c_void_p(_stream(dev)))
     _check("msda_backward", rc)
     return gf, gl, gw
@@ -233,6 +254,7 @@ class BatchedPlan:
     ot: int
     warps: Optional[int] = None
     blocks_per_sm: Optional[int] = None
+    vec: int = 0
     _keep: tuple = ()
 
     def run(self):
@@ -241,13 +263,14 @@ class BatchedPlan:
         rc = lib.msda_forward_batched(_ptr(self.scenes_dev), self.num_scenes, self.total, self.max_ncam,
                                       self.Nscale, self.C, self.P, self.G, self.ft, self.wt, self.ot,
                                       _ptr(self.workspace), self.workspace.numel(), _ptr(self.done_ns),
-                                      _tuning(self.warps, self.blocks_per_sm), ctypes.c_void_p(_stream(dev)))
+                                      _tuning(self.warps, self.blocks_per_sm, 0, self.vec),
+                                      ctypes.c_void_p(_stream(dev)))
         _check("msda_forward_batched", rc)
         return self.outs
 
 
 def plan_batched(scenes: Sequence, out_dtype: torch.dtype = torch.float32, warps: Optional[int] = None,
-                 blocks_per_sm: Optional[int] = None) -> BatchedPlan:
+                 blocks_per_sm: Optional[int] = None, vec: int = 0) -> BatchedPlan:
     """scenes: objects with feat [1,sum_hw,C], spatial_shape, scale_start_index,
     sampling_location [1,A,P,Ncam,2], weights [1,A,P,Ncam,Nscale,G] CUDA tensors."""
     load()
@@ -283,7 +306,7 @@ def plan_batched(scenes: Sequence, out_dtype: torch.dtype = torch.float32, warps
     keep = tuple(t for s in scenes for t in (s.feat, s.spatial_shape, s.scale_start_index,
                                              s.sampling_location, s.weights))
     return BatchedPlan(scenes_dev, ws, done, outs, len(scenes), unit, max_ncam, Nscale, C, P, G,
-                       _DT[fdt], _DT[wdt], _DT[out_dtype], warps, blocks_per_sm, keep)
+                       _DT[fdt], _DT[wdt], _DT[out_dtype], warps, blocks_per_sm, vec, keep)
 
 
 # ---------------------------------------------------------------------------

@@ -55,7 +55,8 @@ def _fwd(lib, **kw):
     vp = ctypes.c_void_p
     return lib.msda_forward(vp(args["feat"]), args["ft"], vp(args["shape"]), vp(args["start"]), vp(args["loc"]),
                             vp(args["w"]), args["wt"], vp(args["out"]), args["ot"], args["B"], args["sum_hw"],
-                            args["C"], args["Ncam"], args["Nscale"], args["A"], args["P"], args["G"], None, None)
+                            args["C"], args["Ncam"], args["Nscale"], args["A"], args["P"], args["G"], None, 0,
+                            None, None)
 
 
 @pytest.mark.parametrize("kw,code", [
@@ -96,6 +97,7 @@ def test_batched_validation(lib):
 
 
 def test_workspace_sizes(lib):
+    assert lib.msda_forward_workspace_size(2, 100, 32, 3, 2, 5, 4, 4) >= 2 * 3 * 5 * 32 * 4
     assert lib.msda_backward_workspace_size(1, 100, 32, 2, 2, 4, 3, 4, 0) == 0
     n = 1 * 4 * 3 * 2 * 2
     ws = lib.msda_backward_workspace_size(1, 100, 32, 2, 2, 4, 3, 4, 1)

@@ -17,10 +17,10 @@ def lib():
     return ensure_lib()
 
 
-def gpu_backward(pr, deterministic, warps=None):
+def gpu_backward(pr, deterministic, warps=None, variant=0):
     d = pr.to("cuda")
     g = msda.backward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights, d.grad_out,
-                      deterministic=deterministic, warps=warps)
+                      deterministic=deterministic, warps=warps, variant=variant)
     torch.cuda.synchronize()
     return [t.cpu() for t in g]
 
@@ -33,54 +33,63 @@ def check_against_oracle(pr, grads, tol, label=""):
     return errs
 
 
-@pytest.mark.parametrize("det", [False, True])
+# (deterministic, variant): atomic scatter, staged deterministic, radix-sort deterministic
+MODES = [(False, 0), (True, 0), (True, 1)]
+
+
+@pytest.mark.parametrize("det,variant", MODES)
 @pytest.mark.parametrize("warps", [1, 4, 8])
-def test_tiny_fp32(det, warps):
+def test_tiny_fp32(det, variant, warps):
     pr = inputs.make_workload(0)
-    check_against_oracle(pr, gpu_backward(pr, det, warps), TOL_FP32, f"tiny det={det} warps={warps}")
+    check_against_oracle(pr, gpu_backward(pr, det, warps, variant), TOL_FP32, f"tiny det={det}/{variant} warps={warps}")
 
 
-@pytest.mark.parametrize("det", [False, True])
-def test_sparse4d_fp32_subset(det):
+@pytest.mark.parametrize("det,variant", MODES)
+def test_sparse4d_fp32_subset(det, variant):
     pr = inputs.make_workload(1).anchors(range(150))
-    check_against_oracle(pr, gpu_backward(pr, det), TOL_FP32, f"sparse4d fp32 det={det}")
+    check_against_oracle(pr, gpu_backward(pr, det, None, variant), TOL_FP32, f"sparse4d fp32 det={det}/{variant}")
 
 
-@pytest.mark.parametrize("det", [False, True])
-def test_train_16cam_bf16_subset(det):
+@pytest.mark.parametrize("det,variant", MODES)
+def test_train_16cam_bf16_subset(det, variant):
     pr = inputs.make_workload(3, batch=2).anchors(range(120))
-    check_against_oracle(pr, gpu_backward(pr, det), TOL_LOWP_GRAD, f"train bf16 det={det}")
+    check_against_oracle(pr, gpu_backward(pr, det, None, variant), TOL_LOWP_GRAD, f"train bf16 det={det}/{variant}")
 
 
 HETERO = [[(5, 7), (3, 4), (2, 2)], [(9, 4), (4, 2), (1, 1)], [(6, 13), (3, 7), (2, 3)]]
 
 
-@pytest.mark.parametrize("C,G,fdt", [(32, 4, "f32"), (64, 8, "bf16"), (128, 2, "f16"), (512, 8, "bf16")])
-@pytest.mark.parametrize("det", [False, True])
-def test_ragged_maps_and_splits(C, G, fdt, det):
+@pytest.mark.parametrize("C,G,fdt", [(32, 4, "f32"), (64, 8, "bf16"), (128, 2, "f16"), (512, 8, "bf16"),
+                                     (256, 32, "bf16"), (256, 2, "f32")])
+@pytest.mark.parametrize("det,variant", MODES)
+def test_ragged_maps_and_splits(C, G, fdt, det, variant):
     gen = torch.Generator().manual_seed(C + G)
     pr = inputs.make_problem(gen, B=2, cam_maps=HETERO, C=C, G=G, A=23, P=5, loc_range=(-0.3, 1.3),
                              feat_dtype=fdt, w_dtype=fdt)
     tol = TOL_FP32 if not is_lowp(pr) else TOL_LOWP_GRAD
-    check_against_oracle(pr, gpu_backward(pr, det), tol, f"ragged C={C} G={G} {fdt} det={det}")
+    check_against_oracle(pr, gpu_backward(pr, det, None, variant), tol, f"ragged C={C} G={G} {fdt} det={det}/{variant}")
 
 
-def test_deterministic_mode_is_bitwise_reproducible():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_deterministic_mode_is_bitwise_reproducible(variant):
     pr = inputs.make_workload(2, ncam=8)
-    a = gpu_backward(pr, True, warps=8)
-    b = gpu_backward(pr, True, warps=8)
-    c = gpu_backward(pr, True, warps=4)
+    a = gpu_backward(pr, True, 8, variant)
+    b = gpu_backward(pr, True, 8, variant)
+    c = gpu_backward(pr, True, 4, variant)
     for x, y, z in zip(a, b, c):
         assert torch.equal(x, y)
         assert torch.equal(x, z)  # every gradient is computed in a fixed order independent of the warps
 
 
-def test_atomic_mode_matches_deterministic():
+def test_all_modes_agree():
     pr = inputs.make_workload(2, ncam=8)
     a = gpu_backward(pr, False)
     d = gpu_backward(pr, True)
-    assert torch.equal(a[1], d[1]) and torch.equal(a[2], d[2])  # dloc, dw: same kernel, no atomics
-    assert relerr(a[0].double().numpy(), d[0].double().numpy()) <= 1e-6
+    r = gpu_backward(pr, True, None, 1)
+    assert torch.equal(a[1], r[1]) and torch.equal(a[2], r[2])  # dloc, dw: same kernel, no atomics
+    for x, y in zip(a, d):
+        assert relerr(x.double().numpy(), y.double().numpy()) <= 1e-6
+    assert relerr(a[0].double().numpy(), r[0].double().numpy()) <= 1e-6
 
 
 def test_outside_in_64cam_full_backward():
@@ -92,8 +101,12 @@ def test_outside_in_64cam_full_backward():
         e = relerr(g.double().numpy(), r)
         print(f"outside-in-64cam {name} rel err {e:.2e}")
         assert e <= TOL_LOWP_GRAD
-    gd = gpu_backward(pr, True)
-    assert relerr(gd[0].double().numpy(), ref[0]) <= TOL_LOWP_GRAD
+    for variant in (0, 1):
+        gd = gpu_backward(pr, True, None, variant)
+        for g, r, name in zip(gd, ref, ["dfeat", "dloc", "dw"]):
+            e = relerr(g.double().numpy(), r)
+            print(f"outside-in-64cam deterministic/{variant} {name} rel err {e:.2e}")
+            assert e <= TOL_LOWP_GRAD
 
 
 def test_train_16cam_full_adjoint_and_sampled_anchors():
@@ -132,10 +145,11 @@ def test_autograd_function_matches_direct_calls_and_gradcheck():
     assert torch.autograd.gradcheck(fn, (f0, w0), eps=1e-2, atol=2e-3, rtol=1e-2, fast_mode=True)
 
 
-def test_out_of_view_points_have_zero_gradients():
+@pytest.mark.parametrize("det,variant", MODES)
+def test_out_of_view_points_have_zero_gradients(det, variant):
     pr = inputs.make_workload(0)
     pr.sampling_location[0, :5, :, :, 0] = 3.0
-    gf, gl, gw = gpu_backward(pr, False)
+    gf, gl, gw = gpu_backward(pr, det, None, variant)
     assert torch.all(gl[0, :5] == 0) and torch.all(gw[0, :5] == 0)
     check_against_oracle(pr, (gf, gl, gw), TOL_FP32, "out of view")
 
@@ -143,6 +157,27 @@ def test_out_of_view_points_have_zero_gradients():
 def test_empty_backward():
     gen = torch.Generator().manual_seed(0)
     pr = inputs.make_problem(gen, B=1, cam_maps=[[(4, 4)]], C=32, G=4, A=0, P=2)
-    for det in (False, True):
-        gf, gl, gw = gpu_backward(pr, det)
+    for det, variant in MODES:
+        gf, gl, gw = gpu_backward(pr, det, None, variant)
         assert torch.all(gf == 0) and gl.numel() == 0 and gw.numel() == 0
+
+
+def test_uncovered_rows_are_zero_and_overlaps_reported():
+    """Rows outside every map get zero gradient; overlapping maps raise the status word (staged mode)."""
+    gen = torch.Generator().manual_seed(3)
+    pr = inputs.make_problem(gen, B=2, cam_maps=[[(6, 5), (3, 2)], [(4, 4), (2, 2)]], C=32, G=4, A=7, P=3)
+    pad = 9
+    feat = torch.cat([pr.feat, torch.randn(2, pad, 32)], dim=1)  # rows no map covers
+    gap = inputs.Problem(feat.contiguous(), pr.spatial_shape, pr.scale_start_index, pr.sampling_location,
+                         pr.weights, pr.grad_out)
+    msda.device_status()
+    for det, variant in MODES:
+        g = gpu_backward(gap, det, None, variant)
+        assert torch.all(g[0][:, -pad:] == 0)
+        check_against_oracle(gap, g, TOL_FP32, f"padded rows det={det}/{variant}")
+    assert msda.device_status() == 0
+    start = pr.scale_start_index.clone()
+    start[1, 0] = 0  # camera 1 scale 0 overlaps camera 0
+    ov = inputs.Problem(pr.feat, pr.spatial_shape, start, pr.sampling_location, pr.weights, pr.grad_out)
+    gpu_backward(ov, True)
+    assert msda.device_status() == 5

@@ -30,7 +30,7 @@ def test_batched_equals_single_scene_calls(warps, bps):
     torch.cuda.synchronize()
     for s, o in zip(scenes, outs):
         single = msda.forward(s.feat, s.spatial_shape, s.scale_start_index, s.sampling_location, s.weights,
-                              warps=warps)
+                              warps=warps, workspace=None)
         assert torch.equal(o, single[0])  # same kernel body, same reduction order
     assert msda.device_status() == 0
 
@@ -77,7 +77,8 @@ def test_full_serving_workload_matches_single_scene_calls():
     outs = plan.run()
     torch.cuda.synchronize()
     for i, (s, o) in enumerate(zip(scenes, outs)):
-        single = msda.forward(s.feat, s.spatial_shape, s.scale_start_index, s.sampling_location, s.weights)
+        single = msda.forward(s.feat, s.spatial_shape, s.scale_start_index, s.sampling_location, s.weights,
+                              workspace=None, warps=8)  # the batched default
         assert torch.equal(o, single[0]), i
     # oracle on sampled anchors of two scenes
     for i in (0, 7):

@@ -17,67 +17,83 @@ def lib():
     return ensure_lib()
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4, 8, 16])
+# the two forward kernels: staged camera-group (workspace) and anchor-per-block (none)
+PATHS = ["auto", None]
+
+
+@pytest.mark.parametrize("warps", [1, 2, 4, 8])
 def test_tiny_fp32_all_tunings(warps):
     pr = inputs.make_workload(0)
-    out = gpu_forward(pr, warps=warps).cpu().double().numpy()
+    out = gpu_forward(pr, warps=warps, workspace=None).cpu().double().numpy()
     ref = oracle_forward(pr)
     assert relerr(out, ref) <= TOL_FP32
 
 
-def test_sparse4d_6cam_fp32_full():
+def test_tiny_fp32_staged():
+    pr = inputs.make_workload(0)
+    assert relerr(gpu_forward(pr).cpu().double().numpy(), oracle_forward(pr)) <= TOL_FP32
+
+
+@pytest.mark.parametrize("ws", PATHS)
+def test_sparse4d_6cam_fp32_full(ws):
     pr = inputs.make_workload(1, with_grad=False)
-    err = relerr(gpu_forward(pr).cpu().double().numpy(), oracle_forward(pr))
-    print(f"sparse4d-6cam FP32 rel err {err:.3e}")
+    err = relerr(gpu_forward(pr, workspace=ws).cpu().double().numpy(), oracle_forward(pr))
+    print(f"sparse4d-6cam FP32 ws={ws} rel err {err:.3e}")
     assert err <= TOL_FP32
 
 
+@pytest.mark.parametrize("ws", PATHS)
 @pytest.mark.parametrize("fdt,wdt", [("bf16", "f32"), ("bf16", "bf16"), ("f16", "f16"), ("f16", "f32")])
-def test_sparse4d_6cam_lowp(fdt, wdt):
+def test_sparse4d_6cam_lowp(fdt, wdt, ws):
     pr = inputs.make_workload(1, feat_dtype=fdt, w_dtype=wdt, with_grad=False)
-    err = relerr(gpu_forward(pr).cpu().double().numpy(), oracle_forward(pr))
+    err = relerr(gpu_forward(pr, workspace=ws).cpu().double().numpy(), oracle_forward(pr))
     print(f"sparse4d-6cam {fdt}/{wdt} rel err {err:.3e}")
     assert err <= TOL_LOWP_OUT
     assert err <= 1e-5  # same rounded inputs on both sides: only FP32 arithmetic differs
 
 
-def test_outside_in_64cam_bf16_full():
+@pytest.mark.parametrize("ws", PATHS)
+def test_outside_in_64cam_bf16_full(ws):
     pr = inputs.make_workload(2, with_grad=False)
-    out = gpu_forward(pr)
+    out = gpu_forward(pr, workspace=ws)
     err = relerr(out.cpu().double().numpy(), oracle_forward(pr))
-    print(f"outside-in-64cam BF16 rel err {err:.3e}")
+    print(f"outside-in-64cam BF16 ws={ws} rel err {err:.3e}")
     assert err <= TOL_LOWP_OUT
-    # launch configuration of the benchmark: bitwise reproducible
-    out2 = gpu_forward(pr)
+    # same launch configuration: bitwise reproducible
+    out2 = gpu_forward(pr, workspace=ws)
     assert torch.equal(out, out2)
 
 
-def test_train_16cam_forward_full():
+@pytest.mark.parametrize("ws", PATHS)
+def test_train_16cam_forward_full(ws):
     pr = inputs.make_workload(3, with_grad=False)
-    err = relerr(gpu_forward(pr).cpu().double().numpy(), oracle_forward(pr))
+    err = relerr(gpu_forward(pr, workspace=ws).cpu().double().numpy(), oracle_forward(pr))
     print(f"train-16cam BF16/FP32 rel err {err:.3e}")
     assert err <= TOL_LOWP_OUT
 
 
+@pytest.mark.parametrize("ws", PATHS)
 @pytest.mark.parametrize("odt", [torch.bfloat16, torch.float16])
-def test_reduced_precision_output_is_rounded_fp32(odt):
+def test_reduced_precision_output_is_rounded_fp32(odt, ws):
     pr = inputs.make_workload(1, feat_dtype="bf16", with_grad=False).anchors(range(200))
-    o32 = gpu_forward(pr)
-    olp = gpu_forward(pr, out_dtype=odt)
+    o32 = gpu_forward(pr, workspace=ws)
+    olp = gpu_forward(pr, out_dtype=odt, workspace=ws)
     assert torch.equal(olp, o32.to(odt))
 
 
 HETERO = [[(5, 7), (3, 4), (2, 2)], [(9, 4), (4, 2), (1, 1)], [(6, 13), (3, 7), (2, 3)]]
 
 
+@pytest.mark.parametrize("ws", PATHS)
 @pytest.mark.parametrize("C,G,fdt", [(32, 4, "f32"), (64, 4, "f32"), (64, 8, "bf16"), (128, 2, "bf16"),
-                                     (512, 8, "bf16"), (1024, 8, "bf16"), (96, 2, "f32"), (48, 3, "bf16")])
-def test_channel_splits_and_ragged_maps(C, G, fdt):
+                                     (512, 8, "bf16"), (1024, 8, "bf16"), (96, 2, "f32"), (48, 3, "bf16"),
+                                     (256, 32, "bf16"), (256, 2, "f32")])
+def test_channel_splits_and_ragged_maps(C, G, fdt, ws):
     gen = torch.Generator().manual_seed(C * 7 + G)
     pr = inputs.make_problem(gen, B=2, cam_maps=HETERO, C=C, G=G, A=37, P=5, loc_range=(-0.3, 1.3),
                              feat_dtype=fdt, w_dtype=fdt, with_grad=False)
     try:
-        out = gpu_forward(pr)
+        out = gpu_forward(pr, workspace=ws)
     except msda.MSDAError as e:
         assert e.code == 2 and (C // G) * (4 if fdt == "f32" else 2) % 16 == 0
         pytest.skip(f"unsupported split reported: {e}")
@@ -100,8 +116,9 @@ def test_many_cameras_and_scales():
     assert relerr(gpu_forward(pr).cpu().double().numpy(), oracle_forward(pr)) <= TOL_LOWP_OUT
 
 
+@pytest.mark.parametrize("ws", PATHS)
 @pytest.mark.parametrize("dims", [dict(A=0), dict(B=0), dict(P=0), dict(Ncam=0)])
-def test_empty_problems(dims):
+def test_empty_problems(dims, ws):
     B, A, P = dims.get("B", 2), dims.get("A", 5), dims.get("P", 3)
     maps = [] if dims.get("Ncam", 1) == 0 else [[(4, 4), (2, 2)]]
     if not maps:
@@ -114,12 +131,13 @@ def test_empty_problems(dims):
     else:
         gen = torch.Generator().manual_seed(0)
         pr = inputs.make_problem(gen, B=B, cam_maps=maps, C=32, G=4, A=A, P=P, with_grad=False)
-    out = gpu_forward(pr)
+    out = gpu_forward(pr, workspace=ws)
     assert out.shape == (B, A, 32)
     assert torch.all(out == 0)
 
 
-def test_nan_inf_and_far_points_contribute_nothing():
+@pytest.mark.parametrize("ws", PATHS)
+def test_nan_inf_and_far_points_contribute_nothing(ws):
     pr = inputs.make_workload(0)
     loc = pr.sampling_location.clone()
     loc[0, 0, 0, 0, 0] = float("nan")
@@ -128,13 +146,14 @@ def test_nan_inf_and_far_points_contribute_nothing():
     loc[0, 3, :, :, 0] = 5.0
     loc[0, 4, :, :, 1] = -1e30
     pr.sampling_location = loc
-    out = gpu_forward(pr).cpu().double().numpy()
+    out = gpu_forward(pr, workspace=ws).cpu().double().numpy()
     ref = oracle_forward(pr)
     assert np.all(out[0, 3] == 0) and np.all(out[0, 4] == 0)
     assert relerr(out, ref) <= TOL_FP32
 
 
-def test_boundary_points_exact_grid():
+@pytest.mark.parametrize("ws", PATHS)
+def test_boundary_points_exact_grid(ws):
     """Points exactly on pixel centres, cell borders and the drop border (-0.5/W, 1+0.5/W)."""
     gen = torch.Generator().manual_seed(9)
     pr = inputs.make_problem(gen, B=1, cam_maps=[[(16, 16), (8, 8)], [(4, 32), (2, 16)]], C=32, G=4, A=8, P=16,
@@ -146,17 +165,18 @@ def test_boundary_points_exact_grid():
         for p in range(16):
             loc[0, a, p, :, 0] = vals[p]
             loc[0, a, p, :, 1] = vals[(p + a) % 16]
-    out = gpu_forward(pr).cpu().double().numpy()
+    out = gpu_forward(pr, workspace=ws).cpu().double().numpy()
     assert relerr(out, oracle_forward(pr)) <= TOL_FP32
 
 
-def test_bad_map_table_is_reported_and_skipped():
+@pytest.mark.parametrize("ws", PATHS)
+def test_bad_map_table_is_reported_and_skipped(ws):
     pr = inputs.make_workload(0)
     start = pr.scale_start_index.clone()
     start[1, 0] = pr.feat.shape[1] - 10  # map would run past sum_hw
     bad = inputs.Problem(pr.feat, pr.spatial_shape, start, pr.sampling_location, pr.weights, None)
     msda.device_status()  # clear
-    out = gpu_forward(bad).cpu().double().numpy()
+    out = gpu_forward(bad, workspace=ws).cpu().double().numpy()
     assert msda.device_status() == 5  # MSDA_ERR_OUT_OF_RANGE
     w = pr.weights.clone()
     w[:, :, :, 1, 0, :] = 0  # the skipped map contributes nothing
@@ -165,15 +185,23 @@ def test_bad_map_table_is_reported_and_skipped():
     assert msda.device_status() == 0
 
 
-def test_anchor_and_camera_permutation_invariance():
+@pytest.mark.parametrize("ws", PATHS)
+def test_anchor_and_camera_permutation_invariance(ws):
     pr = inputs.make_workload(1, feat_dtype="bf16", with_grad=False).anchors(range(64))
-    out = gpu_forward(pr).cpu()
+    out = gpu_forward(pr, workspace=ws).cpu()
     perm = torch.randperm(64, generator=torch.Generator().manual_seed(3))
-    out_p = gpu_forward(pr.anchors(perm)).cpu()
+    out_p = gpu_forward(pr.anchors(perm), workspace=ws).cpu()
     assert torch.equal(out_p, out[:, perm])
     # relabel cameras: permute the tables and the camera axis of loc/weights
     cp = torch.tensor([3, 0, 5, 1, 4, 2])
     pr2 = inputs.Problem(pr.feat, pr.spatial_shape[cp].contiguous(), pr.scale_start_index[cp].contiguous(),
                          pr.sampling_location[:, :, :, cp].contiguous(), pr.weights[:, :, :, cp].contiguous(), None)
-    out_c = gpu_forward(pr2).cpu().double().numpy()
+    out_c = gpu_forward(pr2, workspace=ws).cpu().double().numpy()
     assert relerr(out_c, out.double().numpy()) <= 1e-6  # same terms, different summation order
+
+
+def test_staged_and_anchor_kernels_agree():
+    pr = inputs.make_workload(2, ncam=12, with_grad=False)
+    a = gpu_forward(pr).cpu().double().numpy()
+    b = gpu_forward(pr, workspace=None).cpu().double().numpy()
+    assert relerr(a, b) <= 1e-6
