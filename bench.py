@@ -70,6 +70,15 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(values, device):
+    """Element-wise max of per-rank timings (the job is as slow as its slowest rank)."""
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized() and \
+            torch.distributed.get_world_size() > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -355,10 +364,7 @@ def main():
     total_ms = start.elapsed_time(end)
     fwd_ms = sum(a.elapsed_time(b) for a, b, _ in evs) / args.steps
     bwd_ms = sum(b.elapsed_time(c) for _, b, c in evs) / args.steps
-    t = torch.tensor([total_ms, fwd_ms, bwd_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms, fwd_ms, bwd_ms = t.tolist()
+    total_ms, fwd_ms, bwd_ms = max_over_ranks([total_ms, fwd_ms, bwd_ms], dev)
     ms_per_step = total_ms / args.steps
     if msda.device_status() != 0:
         raise RuntimeError("device status set during the timed region")
@@ -390,10 +396,7 @@ def main():
         e2e_step()
     s1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = torch.tensor([s0.elapsed_time(s1) / args.e2e_steps], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(e2e_ms, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(e2e_ms.item())
+    e2e_ms = max_over_ranks([s0.elapsed_time(s1) / args.e2e_steps], dev)[0]
 
     hbm_peak, peak_src = peaks()
     frames = world * B

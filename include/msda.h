@@ -81,9 +81,9 @@ typedef enum { MSDA_F32 = 0, MSDA_BF16 = 1, MSDA_F16 = 2 } msda_dtype;
 typedef struct {
     int warps_per_block;   /* 1..8: warps per block (teams of lanes per block)   */
     int blocks_per_sm;     /* persistent batched kernel: resident blocks per SM  */
-    int variant;           /* 0 = default; 1 = msda_forward: anchor-per-block
+    int variant;           /* 0 = default; msda_forward: 1 = anchor-per-block
                               kernel even with a workspace; msda_backward
-                              (deterministic): global radix-sort form        */
+                              (deterministic): 2 = staged camera-group form  */
     int vectors_per_lane;  /* 16-byte feature vectors per lane and corner row
                               (1, 2 or 4): more work per lane, fewer lanes
                               per point; 0 = built-in default (forward 2,
@@ -138,16 +138,16 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype,
  *
  *   deterministic = 0: the feature gradient is scattered with FP32 vector
  *     atomics (summation order varies run to run, values agree to rounding).
- *   deterministic = 1: no atomics; bitwise reproducible.  When the staged
- *     kernels apply (Nscale <= 4, C/G a power of two in 4..128, at most
- *     40960 bilinear cells per map, maps that do not overlap, A*(C/G)*4
- *     bytes of grad_out per group fitting in shared memory): dw and dloc
- *     come from the camera-group gather, and the feature gradient from a
- *     stable per-map sort of the points by bilinear cell followed by one
- *     fixed-order gather per feature row.  Otherwise (or with
- *     tuning->variant = 1) the corner contributions are sorted by feature
- *     row with a global stable radix sort and reduced per row.
- *     Overlapping maps raise MSDA_ERR_OUT_OF_RANGE in the status word.
+ *   deterministic = 1: no atomics; bitwise reproducible.  By default the
+ *     corner contributions are sorted by feature row with a global stable
+ *     radix sort and each row is reduced in sorted order.  With
+ *     tuning->variant = 2, when the staged kernels apply (Nscale <= 4, C/G a
+ *     power of two in 4..128, at most 40960 bilinear cells per map, maps
+ *     that do not overlap, A*(C/G)*4 bytes of grad_out per group fitting in
+ *     shared memory): dw and dloc come from the camera-group gather, and the
+ *     feature gradient from a stable per-map sort of the points by bilinear
+ *     cell followed by one fixed-order gather per feature row; overlapping
+ *     maps then raise MSDA_ERR_OUT_OF_RANGE in the status word.
  * grad_loc and grad_weights are computed without atomics in both modes.
  * workspace: device memory of at least msda_backward_workspace_size(...)
  * bytes, 16-byte aligned (may be NULL when that size is 0).

@@ -237,8 +237,8 @@ msda_status msda_backward(const void* feat, msda_dtype feat_dtype, const int32_t
     if (deterministic) {
         if (workspace && !aligned16(workspace))
             return fail(MSDA_ERR_WORKSPACE, "msda_backward: workspace must be 256-byte aligned");
-        const bool sorted_rows = tuning && tuning->variant == 1;  // force the radix-sort form
-        if (!sorted_rows && cg_supported(p))
+        const bool staged = tuning && tuning->variant == 2;  // the staged camera-group form
+        if (staged && cg_supported(p))
             return launch_backward_cg(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes,
                                       (cudaStream_t)stream);
         return launch_backward_det(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes,

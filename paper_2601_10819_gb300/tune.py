@@ -4,7 +4,9 @@ For one problem signature (shapes, dtypes, GPU name) it times every
 candidate mapping of the forward, the backward and the batched forward with
 CUDA events and keeps the fastest.  Results are cached as JSON (path from
 ``MSDA_TUNE_CACHE``, default ``~/.cache/msda_gb300/tune.json``), so a
-signature is searched once per GPU model.  Every candidate computes the same
+signature is searched once per GPU model; signatures measured on GB300 ship
+with the package (``tuned_gb300.json``) and are used when the cache has no
+entry.  Every candidate computes the same
 operator; the mappings differ only in how lanes, warps and blocks are laid
 out (and therefore in the order of FP32 sums).
 """
@@ -32,12 +34,18 @@ def cache_path() -> str:
                                                           "tune.json"))
 
 
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.json")
+
+
 def _load() -> Dict:
-    try:
-        with open(cache_path()) as f:
-            return json.load(f)
-    except Exception:
-        return {}
+    d = {}
+    for path in (SHIPPED, cache_path()):
+        try:
+            with open(path) as f:
+                d.update(json.load(f))
+        except Exception:
+            pass
+    return d
 
 
 def _store(d: Dict):
@@ -91,7 +99,11 @@ def _best(kind: str, sig: str, candidates, run, force: bool) -> Dict:
     results.sort(key=lambda x: x[0])
     best = dict(results[0][1])
     with _lock:
-        cache = _load()
+        try:
+            with open(cache_path()) as f:
+                cache = json.load(f)
+        except Exception:
+            cache = {}
         cache[sig] = {"best": best, "ms": results[0][0],
                       "all": [{"ms": t, **c} for t, c in results]}
         _store(cache)

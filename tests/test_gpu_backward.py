@@ -33,8 +33,8 @@ def check_against_oracle(pr, grads, tol, label=""):
     return errs
 
 
-# (deterministic, variant): atomic scatter, staged deterministic, radix-sort deterministic
-MODES = [(False, 0), (True, 0), (True, 1)]
+# (deterministic, variant): atomic scatter, radix-sort deterministic, staged deterministic
+MODES = [(False, 0), (True, 0), (True, 2)]
 
 
 @pytest.mark.parametrize("det,variant", MODES)
@@ -70,7 +70,7 @@ def test_ragged_maps_and_splits(C, G, fdt, det, variant):
     check_against_oracle(pr, gpu_backward(pr, det, None, variant), tol, f"ragged C={C} G={G} {fdt} det={det}/{variant}")
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 2])
 def test_deterministic_mode_is_bitwise_reproducible(variant):
     pr = inputs.make_workload(2, ncam=8)
     a = gpu_backward(pr, True, 8, variant)
@@ -84,12 +84,12 @@ def test_deterministic_mode_is_bitwise_reproducible(variant):
 def test_all_modes_agree():
     pr = inputs.make_workload(2, ncam=8)
     a = gpu_backward(pr, False)
-    d = gpu_backward(pr, True)
-    r = gpu_backward(pr, True, None, 1)
-    assert torch.equal(a[1], r[1]) and torch.equal(a[2], r[2])  # dloc, dw: same kernel, no atomics
-    for x, y in zip(a, d):
+    d = gpu_backward(pr, True)           # radix-sort rows
+    st = gpu_backward(pr, True, None, 2)  # staged camera-group form
+    assert torch.equal(a[1], d[1]) and torch.equal(a[2], d[2])  # dloc, dw: same kernel, no atomics
+    for x, y, z in zip(a, d, st):
         assert relerr(x.double().numpy(), y.double().numpy()) <= 1e-6
-    assert relerr(a[0].double().numpy(), r[0].double().numpy()) <= 1e-6
+        assert relerr(x.double().numpy(), z.double().numpy()) <= 1e-6
 
 
 def test_outside_in_64cam_full_backward():
@@ -101,7 +101,7 @@ def test_outside_in_64cam_full_backward():
         e = relerr(g.double().numpy(), r)
         print(f"outside-in-64cam {name} rel err {e:.2e}")
         assert e <= TOL_LOWP_GRAD
-    for variant in (0, 1):
+    for variant in (0, 2):
         gd = gpu_backward(pr, True, None, variant)
         for g, r, name in zip(gd, ref, ["dfeat", "dloc", "dw"]):
             e = relerr(g.double().numpy(), r)
@@ -179,5 +179,8 @@ def test_uncovered_rows_are_zero_and_overlaps_reported():
     start = pr.scale_start_index.clone()
     start[1, 0] = 0  # camera 1 scale 0 overlaps camera 0
     ov = inputs.Problem(pr.feat, pr.spatial_shape, start, pr.sampling_location, pr.weights, pr.grad_out)
-    gpu_backward(ov, True)
+    gpu_backward(ov, True, None, 2)  # the staged form needs disjoint maps and reports the overlap
     assert msda.device_status() == 5
+    g = gpu_backward(ov, True)  # the radix form handles overlapping maps
+    check_against_oracle(ov, g, TOL_FP32, "overlapping maps, radix form")
+    assert msda.device_status() == 0
