@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deterministic", action="store_true", help="time the deterministic backward instead")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in launch mappings")
+    ap.add_argument("--extras", action="store_true",
+                    help="also time the fused occlusion-aware forward, the keypoint prologue and the half2 forward")
     ap.add_argument("--with-batched", action="store_true",
                     help="also time the 16-scene batched serving workload (per-scene p50/p99)")
     return ap.parse_args()
@@ -228,6 +230,43 @@ def batched_serving(dev, stream, tune_it=True, reps=20):
             "gsamples_per_s": nominal / (statistics.median(total) * 1e-6) / 1e9}
 
 
+def extras(pr, dev, ft, reps=20):
+    """Timings (us) of the other forms of the path on the benchmark frame."""
+    from paper_2601_10819_gb300 import inputs, msda
+    d = pr.to(dev)
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    out = torch.empty(d.grad_out.shape, device=dev)
+    vis = inputs.make_visibility(pr, 2).to(dev)
+    geo = [t.to(dev) for t in inputs.make_scene_geometry(2, B=1, A=pr.weights.shape[1], P=pr.weights.shape[2],
+                                                         ncam=pr.weights.shape[3])]
+    loc = torch.empty_like(d.sampling_location)
+    f16 = (d.feat.half(), d.weights.half())
+
+    def tm(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps * 1e3
+
+    kw = dict(warps=ft["warps"] or None, vec=ft["vec"])
+    return {
+        "forward_us": tm(lambda: msda.forward(*T, out=out, workspace=None, **kw)),
+        "forward_fused_occlusion_aware_us": tm(lambda: msda.forward_oae(*T, vis, out=out, **kw)),
+        "keypoint_prologue_us": tm(lambda: msda.keypoints(*geo, out=loc)),
+        "forward_fp16_fp32acc_us": tm(lambda: msda.forward(f16[0], d.spatial_shape, d.scale_start_index,
+                                                           d.sampling_location, f16[1], out=out, workspace=None, **kw)),
+        "forward_fp16_half2acc_us": tm(lambda: msda.forward(f16[0], d.spatial_shape, d.scale_start_index,
+                                                            d.sampling_location, f16[1], out=out, workspace=None,
+                                                            variant=3, **kw)),
+    }
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle, timed on the host cores."""
     if rank != 0:
@@ -313,13 +352,21 @@ def main():
         ft = tune.tune_forward(tensors, out, workspace=fws)
         bt = tune.tune_backward(tensors, d.grad_out, (gf, gl, gw), deterministic=det, workspace=ws)
     fwd_ws = fws if ft["workspace"] else None
+    side = torch.cuda.Stream(dev)  # clears the feature gradient while the forward runs (atomic mode)
+    main = torch.cuda.current_stream(dev)
 
-    def fwd():
-        msda.forward(*tensors, out=out, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
+    def fwd(tens=None):
+        if not det:
+            side.wait_stream(main)  # the previous backward is done with grad_feat
+            with torch.cuda.stream(side):
+                gf.zero_()
+        msda.forward(*(tens or tensors), out=out, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
 
-    def bwd():
-        msda.backward(*tensors, d.grad_out, deterministic=det, workspace=ws, grads=(gf, gl, gw),
-                      warps=bt["warps"] or None, vec=bt["vec"])
+    def bwd(tens=None, go=None):
+        if not det:
+            main.wait_stream(side)
+        msda.backward(*(tens or tensors), d.grad_out if go is None else go, deterministic=det, workspace=ws,
+                      grads=(gf, gl, gw), warps=bt["warps"] or None, vec=bt["vec"], grad_feat_zeroed=not det)
 
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -380,9 +427,8 @@ def main():
         for h, dd in zip(h_in, d_in):
             dd.copy_(h, non_blocking=True)
         tens = (d_in[0], d.spatial_shape, d.scale_start_index, d_in[1], d_in[2])
-        msda.forward(*tens, out=out, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
-        msda.backward(*tens, d_in[3], deterministic=det, workspace=ws, grads=(gf, gl, gw),
-                      warps=bt["warps"] or None, vec=bt["vec"])
+        fwd(tens)
+        bwd(tens, d_in[3])
         for h, dd in zip(h_out, (out, gf, gl, gw)):
             h.copy_(dd, non_blocking=True)
 
@@ -419,6 +465,7 @@ def main():
         "vs_baseline": None, "dtype": "bf16", "accumulate": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": B, "parallelism": f"replicas x{world}",
                    "backward": "deterministic" if det else "atomic",
+                   "overlap": None if det else "feature gradient cleared on a side stream during the forward",
                    "l2": "inputs larger than L2 (feat 355 MB, grad_feat 710 MB per frame); no flush"},
         "gsamples_per_s": cnt.nominal_samples * frames / (ms_per_step * 1e-3) / 1e9,
         "inview_gsamples_per_s": cnt.inview_samples * frames / (ms_per_step * 1e-3) / 1e9,
@@ -441,6 +488,8 @@ def main():
     }
     if args.with_batched:
         line["batched_serving"] = batched_serving(dev, stream, tune_it=not args.no_tune)
+    if args.extras:
+        line["extras"] = extras(pr, dev, ft)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, args.cpu_sample_anchors)
     if rank == 0:

@@ -82,14 +82,24 @@ typedef struct {
     int warps_per_block;   /* 1..8: warps per block (teams of lanes per block)   */
     int blocks_per_sm;     /* persistent batched kernel: resident blocks per SM  */
     int variant;           /* 0 = default; msda_forward: 1 = anchor-per-block
-                              kernel even with a workspace; msda_backward
-                              (deterministic): 2 = staged camera-group form  */
+                              kernel even with a workspace, 3 = FP16
+                              features and weights accumulated in half2 (the
+                              paper's plugin arithmetic, Sec. 5.3; less
+                              accurate); msda_backward (deterministic):
+                              2 = staged camera-group form                   */
     int vectors_per_lane;  /* 16-byte feature vectors per lane and corner row
                               (1, 2 or 4): more work per lane, fewer lanes
                               per point; 0 = built-in default (forward 2,
                               backward 1), else the smallest valid split     */
-    int reserved[4];
+    int flags;             /* MSDA_FLAG_* bits                                */
+    int reserved[3];
 } msda_tuning;
+
+/* tuning->flags: the caller has already zeroed grad_feat (for example on a
+ * side stream while the forward ran); the atomic backward then skips its
+ * own clearing of grad_feat.  Ignored by the deterministic modes, which
+ * write every row. */
+#define MSDA_FLAG_GRAD_FEAT_ZEROED 1
 
 /* ------------------------------------------------------------------------
  * msda_forward - the operator above (Sec. 3.2 multi-scale multi-view
@@ -122,6 +132,44 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype,
                          const msda_tuning* tuning, msda_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * msda_forward_oae - the operator followed by the occlusion-aware
+ * visibility-weighted fusion over cameras (Sec. 3.2, Eq. 2), fused:
+ *   out[b,a,:] = sum_k vis[b,a,k] * g_k / sum_k vis[b,a,k]
+ * where g_k is the operator above restricted to camera k.  Implemented by
+ * scaling every weight of camera k by vis[b,a,k] / sum_j vis[b,a,j] inside
+ * the anchor-per-block forward (cameras with zero visibility are skipped).
+ * An anchor whose visibilities sum to 0 gets out = 0.
+ *   visibility: [B, A, Ncam] float32, device, 16-byte aligned.
+ * Other arguments and errors as msda_forward (no workspace).
+ * ------------------------------------------------------------------------ */
+msda_status msda_forward_oae(const void* feat, msda_dtype feat_dtype,
+                             const int32_t* spatial_shape, const int32_t* scale_start_index,
+                             const float* sampling_location,
+                             const void* weights, msda_dtype weights_dtype,
+                             const float* visibility,
+                             void* out, msda_dtype out_dtype,
+                             int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,
+                             const msda_tuning* tuning, msda_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * msda_keypoints - the sampling locations the operator consumes (Sec. 3.1
+ * and 3.2: anchor keypoints, motion compensation with the estimated
+ * velocity, projection into every camera):
+ *   q = R(yaw) (offset * (w, l, h)) + centre + velocity * dt
+ *   (hx, hy, hz) = proj_k (q, 1)
+ *   sampling_location[b,a,p,k] = (hx/hz/width_k, hy/hz/height_k),
+ *                                or (-2, -2) when hz <= 1e-5.
+ *   anchors [B, A, 11] = (x, y, z, w, l, h, sin yaw, cos yaw, vx, vy, vz)
+ *   offsets [B, A, P, 3] keypoints in box units; dt [B];
+ *   proj [B, Ncam, 3, 4] world -> homogeneous pixels; img_wh [Ncam, 2];
+ *   sampling_location [B, A, P, Ncam, 2] written.  All float32, device,
+ *   16-byte aligned.
+ * ------------------------------------------------------------------------ */
+msda_status msda_keypoints(const float* anchors, const float* offsets, const float* dt,
+                           const float* proj, const float* img_wh, float* sampling_location,
+                           int B, int A, int P, int Ncam, msda_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * msda_backward - gradients of msda_forward for the upstream gradient
  * grad_out [B, A, C] (float32):
  *   grad_feat    [B, sum_hw, C]             float32, overwritten
@@ -138,6 +186,9 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype,
  *
  *   deterministic = 0: the feature gradient is scattered with FP32 vector
  *     atomics (summation order varies run to run, values agree to rounding).
+ *     With a workspace (256 bytes) the items are handed out from one
+ *     counter strictly in camera order, which keeps the rows being
+ *     accumulated in L2; with workspace = NULL a static stride is used.
  *   deterministic = 1: no atomics; bitwise reproducible.  By default the
  *     corner contributions are sorted by feature row with a global stable
  *     radix sort and each row is reduced in sorted order.  With

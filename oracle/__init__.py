@@ -69,6 +69,10 @@ def load_library(path: str):
     lib.msda_oracle_forward.restype = i
     lib.msda_oracle_backward.argtypes = [dp, ip, ip, dp, dp, dp, dp, dp, dp] + [i] * 8
     lib.msda_oracle_backward.restype = i
+    lib.msda_oracle_forward_oae.argtypes = [dp, ip, ip, dp, dp, dp, dp] + [i] * 8
+    lib.msda_oracle_forward_oae.restype = i
+    lib.msda_oracle_keypoints.argtypes = [dp, dp, dp, dp, dp, dp] + [i] * 4
+    lib.msda_oracle_keypoints.restype = i
     lib.msda_oracle_max_threads.argtypes = []
     lib.msda_oracle_max_threads.restype = i
     return lib
@@ -149,6 +153,46 @@ def backward(feat, spatial_shape, scale_start_index, sampling_location, weights,
     if rc != 0:
         raise ValueError("oracle backward rejected its arguments")
     return gf, gl, gw
+
+
+def forward_oae(feat, spatial_shape, scale_start_index, sampling_location, weights, visibility,
+                lib=None) -> np.ndarray:
+    """Visibility-weighted fusion over cameras (Sec. 3.2, Eq. 2); see msda_oracle.c."""
+    lib = lib or _get_lib()
+    feat, loc, w = _f64(feat), _f64(sampling_location), _f64(weights)
+    vis = _f64(visibility)
+    shape, start = _i32(spatial_shape), _i32(scale_start_index)
+    G = w.shape[-1]
+    B, sum_hw, C, Ncam, Nscale, A, P = _dims(feat, shape, loc, w, G)
+    if vis.shape != (B, A, Ncam):
+        raise ValueError("visibility must be [B, A, Ncam]")
+    out = np.zeros((B, A, C), dtype=np.float64)
+    rc = lib.msda_oracle_forward_oae(
+        _ptr(feat, ctypes.c_double), _ptr(shape, ctypes.c_int32), _ptr(start, ctypes.c_int32),
+        _ptr(loc, ctypes.c_double), _ptr(w, ctypes.c_double), _ptr(vis, ctypes.c_double),
+        _ptr(out, ctypes.c_double), B, sum_hw, C, Ncam, Nscale, A, P, G)
+    if rc != 0:
+        raise ValueError("oracle forward_oae rejected its arguments")
+    return out
+
+
+def keypoints(anchors, offsets, dt, proj, img_wh, lib=None) -> np.ndarray:
+    """Sampling locations [B, A, P, Ncam, 2] of the keypoint prologue; see msda_oracle.c."""
+    lib = lib or _get_lib()
+    an, of, dtt, pr, wh = _f64(anchors), _f64(offsets), _f64(dt), _f64(proj), _f64(img_wh)
+    B, A, _ = an.shape
+    P = of.shape[2]
+    Ncam = pr.shape[1]
+    if an.shape[2] != 11 or of.shape != (B, A, P, 3) or dtt.shape != (B,) or pr.shape != (B, Ncam, 3, 4) \
+            or wh.shape != (Ncam, 2):
+        raise ValueError("bad keypoint prologue shapes")
+    loc = np.zeros((B, A, P, Ncam, 2), dtype=np.float64)
+    rc = lib.msda_oracle_keypoints(_ptr(an, ctypes.c_double), _ptr(of, ctypes.c_double), _ptr(dtt, ctypes.c_double),
+                                   _ptr(pr, ctypes.c_double), _ptr(wh, ctypes.c_double), _ptr(loc, ctypes.c_double),
+                                   B, A, P, Ncam)
+    if rc != 0:
+        raise ValueError("oracle keypoints rejected its arguments")
+    return loc
 
 
 def max_threads(lib=None) -> int:

@@ -57,6 +57,7 @@
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -209,6 +210,106 @@ int msda_oracle_backward(const double* feat, const int32_t* shape, const int32_t
                 grad_loc[pk * 2 + 1] = dv;
             }
     }
+    return 0;
+}
+
+/* Occlusion-aware fusion (Sec. 3.2, Eq. 2): the per-camera aggregated
+ * feature g_k = sum_{p,s} w[b,a,p,k,s,g] * S_{b,k,s}(loc[b,a,p,k]) is fused
+ * over cameras with the visibility scores vis[b, a, k]:
+ *   out[b,a,c] = sum_k vis[b,a,k] * g_k[c] / sum_k vis[b,a,k]
+ * Reading: when the visibilities of an anchor sum to 0 the fused feature is
+ * 0.  Computed literally: each g_k by the forward above restricted to camera
+ * k, then the weighted mean.  Returns 0, or 1 on bad arguments. */
+int msda_oracle_forward_oae(const double* feat, const int32_t* shape, const int32_t* start,
+                            const double* loc, const double* w, const double* vis, double* out,
+                            int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G)
+{
+    if (check_dims(B, sum_hw, C, Ncam, Nscale, A, P, G)) return 1;
+    if (check_tables(shape, start, sum_hw, Ncam, Nscale)) return 1;
+    const int Cg = C / G;
+    const long BA = (long)B * A;
+    double* g = (double*)malloc(sizeof(double) * (size_t)C);
+    if (!g) return 1;
+    for (long ba = 0; ba < BA; ++ba) {
+        const long b = ba / A;
+        double* o = out + ba * C;
+        double vsum = 0.0;
+        for (int k = 0; k < Ncam; ++k) vsum += vis[ba * Ncam + k];
+        for (int c = 0; c < C; ++c) o[c] = 0.0;
+        if (vsum == 0.0) continue;
+        for (int k = 0; k < Ncam; ++k) {
+            for (int c = 0; c < C; ++c) g[c] = 0.0;
+            for (int p = 0; p < P; ++p) {
+                const double* uv = loc + ((ba * P + p) * Ncam + k) * 2;
+                for (int s = 0; s < Nscale; ++s) {
+                    const int H = shape[(k * Nscale + s) * 2 + 0];
+                    const int W = shape[(k * Nscale + s) * 2 + 1];
+                    const long row0 = b * (long)sum_hw + start[k * Nscale + s];
+                    corners_t cr = locate(uv[0], uv[1], H, W, row0);
+                    if (!cr.in_range) continue;
+                    const double* wg = w + (((ba * P + p) * Ncam + k) * Nscale + s) * G;
+                    for (int q = 0; q < 4; ++q) {
+                        if (!cr.valid[q]) continue;
+                        const double* f = feat + cr.row[q] * (long)C;
+                        for (int c = 0; c < C; ++c) g[c] += wg[c / Cg] * cr.omega[q] * f[c];
+                    }
+                }
+            }
+            const double vk = vis[ba * Ncam + k];
+            for (int c = 0; c < C; ++c) o[c] += vk * g[c];
+        }
+        for (int c = 0; c < C; ++c) o[c] /= vsum;
+    }
+    free(g);
+    return 0;
+}
+
+/* Keypoint prologue (Sec. 3.1, 3.2): the sampling locations of every
+ * anchor keypoint in every camera.
+ *   anchors [B, A, 11] = (x, y, z, w, l, h, sin yaw, cos yaw, vx, vy, vz),
+ *     box centre and velocity in the world frame, sizes along the box's
+ *     x (w), y (l) and z (h) axes;
+ *   offsets [B, A, P, 3] keypoints in box units (fixed and learned alike);
+ *   dt [B]: time from the anchor's frame to the current frame;
+ *   proj [B, Ncam, 3, 4]: world -> homogeneous pixel matrix of each camera;
+ *   img_wh [Ncam, 2]: image width and height in pixels.
+ * Keypoint (Sec. 3.2: motion-compensated with the estimated velocity):
+ *   q = R(yaw) (offset * size) + centre + velocity * dt
+ * Projection: (xp, yp, zp) = proj * (q, 1); loc = (xp / zp / width,
+ * yp / zp / height).  Reading: a keypoint with zp <= 1e-5 (behind or on the
+ * camera plane) gets loc = (-2, -2), which the operator drops. */
+int msda_oracle_keypoints(const double* anchors, const double* offsets, const double* dt,
+                          const double* proj, const double* img_wh, double* loc,
+                          int B, int A, int P, int Ncam)
+{
+    if (B < 0 || A < 0 || P < 0 || Ncam < 0) return 1;
+    for (long b = 0; b < B; ++b)
+        for (long a = 0; a < A; ++a) {
+            const double* an = anchors + (b * A + a) * 11;
+            const double sy = an[6], cy = an[7];
+            for (long p = 0; p < P; ++p) {
+                const double* of = offsets + ((b * A + a) * P + p) * 3;
+                const double bx = of[0] * an[3], by = of[1] * an[4], bz = of[2] * an[5];
+                double q[3];
+                q[0] = cy * bx - sy * by + an[0] + an[8] * dt[b];
+                q[1] = sy * bx + cy * by + an[1] + an[9] * dt[b];
+                q[2] = bz + an[2] + an[10] * dt[b];
+                for (long k = 0; k < Ncam; ++k) {
+                    const double* M = proj + (b * Ncam + k) * 12;
+                    double h[3];
+                    for (int r = 0; r < 3; ++r)
+                        h[r] = M[r * 4 + 0] * q[0] + M[r * 4 + 1] * q[1] + M[r * 4 + 2] * q[2] + M[r * 4 + 3];
+                    double* o = loc + (((b * A + a) * P + p) * Ncam + k) * 2;
+                    if (h[2] <= 1e-5) {
+                        o[0] = -2.0;
+                        o[1] = -2.0;
+                    } else {
+                        o[0] = h[0] / h[2] / img_wh[k * 2 + 0];
+                        o[1] = h[1] / h[2] / img_wh[k * 2 + 1];
+                    }
+                }
+            }
+        }
     return 0;
 }
 

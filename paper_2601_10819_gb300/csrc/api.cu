@@ -193,18 +193,40 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype, const int32_t*
     if ((long long)B * A > 0 && !out) return fail(MSDA_ERR_INVALID_ARG, "msda_forward: out is NULL");
     if (!aligned16(out)) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: out must be 16-byte aligned");
     prefer_split(tuning, &p, 2);
-    const bool direct = tuning && tuning->variant == 1;  // force the anchor-per-block kernel
+    const bool half_acc = tuning && tuning->variant == 3;  // paper-faithful half2 accumulation
+    const bool direct = tuning && (tuning->variant == 1 || half_acc);  // force the anchor-per-block kernel
     if (workspace && !direct && cg_supported(p)) {
         if (!aligned16(workspace)) return fail(MSDA_ERR_WORKSPACE, "msda_forward: workspace must be 16-byte aligned");
         return launch_forward_cg(p, out, out_dtype, workspace, workspace_bytes, (cudaStream_t)stream);
     }
-    return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream);
+    return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream, nullptr, half_acc);
+}
+
+msda_status msda_forward_oae(const void* feat, msda_dtype feat_dtype, const int32_t* spatial_shape,
+                             const int32_t* scale_start_index, const float* sampling_location,
+                             const void* weights, msda_dtype weights_dtype, const float* visibility, void* out,
+                             msda_dtype out_dtype, int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P,
+                             int G, const msda_tuning* tuning, msda_stream_t stream) {
+    t_err[0] = 0;
+    Problem p;
+    msda_status st = validate("msda_forward_oae", feat, feat_dtype, spatial_shape, scale_start_index,
+                              sampling_location, weights, weights_dtype, B, sum_hw, C, Ncam, Nscale, A, P, G, &p);
+    if (st != MSDA_OK) return st;
+    if (dtype_size(out_dtype) == 0) return fail(MSDA_ERR_INVALID_ARG, "msda_forward_oae: unknown out dtype");
+    if ((long long)B * A > 0 && !out) return fail(MSDA_ERR_INVALID_ARG, "msda_forward_oae: out is NULL");
+    if ((long long)B * A * Ncam > 0 && !visibility)
+        return fail(MSDA_ERR_INVALID_ARG, "msda_forward_oae: visibility is NULL");
+    if (!aligned16(out) || !aligned16(visibility))
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_oae: out and visibility must be 16-byte aligned");
+    prefer_split(tuning, &p, 2);
+    return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream,
+                          visibility ? visibility : nullptr);
 }
 
 size_t msda_backward_workspace_size(int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,
                                     int deterministic) {
-    if (!deterministic || B < 0 || sum_hw < 0 || C < 1 || Ncam < 0 || Nscale < 0 || A < 0 || P < 0 || G < 1)
-        return 0;
+    if (B < 0 || sum_hw < 0 || C < 1 || Ncam < 0 || Nscale < 0 || A < 0 || P < 0 || G < 1) return 0;
+    if (!deterministic) return 256;  // the work counter of the dynamic item order
     Problem p;
     p.B = B; p.sum_hw = sum_hw; p.C = C; p.Ncam = Ncam; p.Nscale = Nscale; p.A = A; p.P = P; p.G = G;
     p.Cg = C / G;
@@ -244,7 +266,11 @@ msda_status msda_backward(const void* feat, msda_dtype feat_dtype, const int32_t
         return launch_backward_det(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes,
                                    warps, (cudaStream_t)stream);
     }
-    return launch_backward_atomic(p, grad_out, grad_feat, grad_loc, grad_weights, warps, (cudaStream_t)stream);
+    if (workspace && !aligned16(workspace))
+        return fail(MSDA_ERR_WORKSPACE, "msda_backward: workspace must be 16-byte aligned");
+    const bool zeroed = tuning && (tuning->flags & MSDA_FLAG_GRAD_FEAT_ZEROED);
+    return launch_backward_atomic(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes, warps,
+                                  zeroed, (cudaStream_t)stream);
 }
 
 size_t msda_forward_batched_workspace_size(int num_scenes) {
@@ -305,6 +331,21 @@ msda_status msda_forward_batched_noalloc(const msda_scene* scenes, int num_scene
                                           tuning ? tuning->blocks_per_sm : 0,
                                           tuning && tuning->vectors_per_lane > 0 ? tuning->vectors_per_lane : 2,
                                           (cudaStream_t)stream);
+}
+
+msda_status msda_keypoints(const float* anchors, const float* offsets, const float* dt, const float* proj,
+                           const float* img_wh, float* sampling_location, int B, int A, int P, int Ncam,
+                           msda_stream_t stream) {
+    t_err[0] = 0;
+    if (B < 0 || A < 0 || P < 0 || Ncam < 0) return fail(MSDA_ERR_INVALID_ARG, "msda_keypoints: negative dimension");
+    const long long n = (long long)B * A * P * Ncam;
+    if (n > 0 && (!anchors || !offsets || !dt || !proj || !img_wh || !sampling_location))
+        return fail(MSDA_ERR_INVALID_ARG, "msda_keypoints: NULL pointer");
+    if (!aligned16(anchors) || !aligned16(offsets) || !aligned16(dt) || !aligned16(proj) || !aligned16(img_wh) ||
+        !aligned16(sampling_location))
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_keypoints: pointers must be 16-byte aligned");
+    return launch_keypoints(anchors, offsets, dt, proj, img_wh, sampling_location, B, A, P, Ncam,
+                            (cudaStream_t)stream);
 }
 
 msda_status msda_get_device_status(msda_stream_t stream) {

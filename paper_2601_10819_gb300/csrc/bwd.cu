@@ -37,9 +37,12 @@ struct BwdArgs {
     float* gw;
     int B, sum_hw, C, Ncam, Nscale, A, P, G, Cg;
     int rt;
-    int scatter;  // 0: skip the feature-gradient atomics (deterministic mode)
+    int scatter;  // 0: skip the feature-gradient atomics (deterministic mode); 1, 2: scatter
+    unsigned long long* counter;  // next unhanded item (dynamic order) or NULL (static stride)
     int* status;
 };
+
+constexpr int kItemsPerGrab = 4;  // items per team taken from the counter at once
 
 __device__ __forceinline__ float4 scale4(float a, const float4& v) {
     return make_float4(a * v.x, a * v.y, a * v.z, a * v.w);
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
     const long long nitems = (long long)p.Ncam * per_cam;
     const long long total_teams = (long long)gridDim.x * nteams;
     // Global item list ordered (camera, anchor, keypoint); all teams walk it together.
-    for (long long item = (long long)blockIdx.x * nteams + team; item < nitems; item += total_teams) {
+    auto process = [&](long long item) {
         const int k = (int)(item / per_cam);
         const long long r = item - (long long)k * per_cam;
         const long long ba = r / p.P;
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
             if ((tl & (lg - 1)) == 0)
                 for (int s = 0; s < p.Nscale; ++s) gwrow[(long long)s * p.G] = 0.0f;
             if (tl == 0) reinterpret_cast<float2*>(p.gloc)[pk] = make_float2(0.0f, 0.0f);
-            continue;
+            return;
         }
         const float* gorow = p.go + ba * p.C;
         float2 go[CPL / 2];
@@ -189,6 +192,25 @@ __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
         du = team_sum(du, tmask, p.rt);
         dv = team_sum(dv, tmask, p.rt);
         if (tl == 0) reinterpret_cast<float2*>(p.gloc)[pk] = make_float2(du, dv);
+        };
+    if (p.counter) {
+        // dynamic order: each block takes the next kItemsPerGrab items per team from one counter, so
+        // items are handed out strictly in camera order and no team runs ahead of the others
+        __shared__ unsigned long long s_base;
+        const unsigned long long chunk = (unsigned long long)nteams * kItemsPerGrab;
+        for (;;) {
+            if (threadIdx.x == 0) s_base = atomicAdd(p.counter, chunk);
+            __syncthreads();
+            const unsigned long long base = s_base;
+            __syncthreads();
+            if (base >= (unsigned long long)nitems) break;
+            for (int j = 0; j < kItemsPerGrab; ++j) {
+                const long long item = (long long)base + (long long)j * nteams + team;
+                if (item < nitems) process(item);
+            }
+        }
+    } else {
+        for (long long item = (long long)blockIdx.x * nteams + team; item < nitems; item += total_teams) process(item);
     }
 }
 
@@ -218,20 +240,23 @@ size_t bwd_smem_bytes(const Problem& p) {
 }
 
 msda_status launch_backward_atomic(const Problem& p, const float* grad_out, float* grad_feat,
-                                   float* grad_loc, float* grad_w, int warps, cudaStream_t stream) {
-    return launch_backward_loc_w(p, grad_out, grad_feat, grad_loc, grad_w, warps, 1, stream);
+                                   float* grad_loc, float* grad_w, void* ws, size_t ws_bytes, int warps,
+                                   bool zeroed, cudaStream_t stream) {
+    unsigned long long* counter = (ws && ws_bytes >= sizeof(unsigned long long))
+                                      ? reinterpret_cast<unsigned long long*>(ws) : nullptr;
+    return launch_backward_loc_w(p, grad_out, grad_feat, grad_loc, grad_w, warps, zeroed ? 2 : 1, stream, counter);
 }
 
 msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float* grad_feat,
                                   float* grad_loc, float* grad_w, int warps, int scatter,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, unsigned long long* counter) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);
     if (st != MSDA_OK) return st;
     BwdKernel k = bwd_kernel_for(p.feat_t, p.w_t, p.nv);
     if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: unsupported feature/weight dtype pair");
     const size_t feat_bytes = sizeof(float) * (size_t)p.B * p.sum_hw * p.C;
-    if (scatter && feat_bytes && cudaMemsetAsync(grad_feat, 0, feat_bytes, stream) != cudaSuccess)
+    if (scatter == 1 && feat_bytes && cudaMemsetAsync(grad_feat, 0, feat_bytes, stream) != cudaSuccess)
         return check_launch("msda_backward memset");
     const long long nblocks = (long long)p.B * p.A;
     if (nblocks == 0) return MSDA_OK;
@@ -243,6 +268,9 @@ msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float
     a.go = grad_out; a.gfeat = grad_feat; a.gloc = grad_loc; a.gw = grad_w;
     a.B = p.B; a.sum_hw = p.sum_hw; a.C = p.C; a.Ncam = p.Ncam; a.Nscale = p.Nscale;
     a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.scatter = scatter; a.status = dev.status;
+    a.counter = counter;
+    if (counter && cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+        return check_launch("msda_backward counter");
     // persistent grid: as many blocks as fit at once, all walking one camera-major item list
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, warps * 32, smem) != cudaSuccess || occ < 1)

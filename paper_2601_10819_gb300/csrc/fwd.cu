@@ -35,6 +35,7 @@ struct FwdArgs {
     const int32_t* start;
     const float* loc;
     const void* w;
+    const float* vis;  // visibility [B, A, Ncam] for the fused occlusion-aware form, or NULL
     void* out;
     int out_t;
     int B, sum_hw, C, Ncam, Nscale, A, P, G, Cg;
@@ -44,11 +45,12 @@ struct FwdArgs {
 
 // Shared-memory carve-up of a forward block.
 struct FwdSmem {
-    size_t maps, box, loc, part, total;
+    size_t maps, box, vn, loc, part, total;
     __host__ __device__ FwdSmem(int nmaps, int P, int Ncam, int nteams, int C) {
         maps = 0;
         box = align16(sizeof(MapInfo) * (size_t)nmaps);
-        loc = box + sizeof(float4) * (size_t)Ncam;
+        vn = box + sizeof(float4) * (size_t)Ncam;
+        loc = vn + align16(sizeof(float) * (size_t)Ncam);
         part = loc + align16(sizeof(float2) * (size_t)P * Ncam);
         total = part + sizeof(float) * (size_t)nteams * C;
     }
@@ -60,12 +62,15 @@ struct FwdSmem {
 // Items outside the camera's box are skipped with one test.  Per scale, the
 // four corner rows are loaded (NV 16-byte chunks each; unpredicated when the
 // cell is inside the map) and accumulated with packed FP32 FMAs.
+// svn (optional): per-camera factor applied to every weight of the camera
+// (the normalised visibility of the fused occlusion-aware form); a camera
+// with factor 0 is skipped.
 template <typename FT, typename WT, int NV>
 __device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, const WT* __restrict__ wb,
                                                   const MapInfo* __restrict__ smap, const float4* __restrict__ sbox,
                                                   const float2* __restrict__ sloc, int C, int Ncam,
                                                   int Nscale, int P, int G, int team, int nteams,
-                                                  float2* acc) {
+                                                  float2* acc, const float* __restrict__ svn = nullptr) {
     constexpr int VEC = Elem<FT>::VEC;
     const int nitems = Ncam * P;
     for (int item = team; item < nitems; item += nteams) {
@@ -73,13 +78,15 @@ __device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, con
         const int pp = item - k * P;
         const float2 uv = sloc[pp * Ncam + k];
         if (!in_box(uv, sbox[k])) continue;
+        const float cam_scale = svn ? svn[k] : 1.0f;
+        if (cam_scale == 0.0f) continue;
         const WT* wrow = wb + ((long long)pp * Ncam + k) * Nscale * G;
         const MapInfo* mrow = smap + k * Nscale;
         for (int s = 0; s < Nscale; ++s) {
             const MapInfo m = mrow[s];
             Cell c;
             if (m.W == 0 || !locate(uv.x, uv.y, m.H, m.W, c)) continue;
-            const float wv = ldw(wrow + (long long)s * G);
+            const float wv = ldw(wrow + (long long)s * G) * cam_scale;
             const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
             const float2 w00 = make_float2(wv * (ax * ay), wv * (ax * ay));
             const float2 w01 = make_float2(wv * (c.fx * ay), wv * (c.fx * ay));
@@ -148,7 +155,7 @@ __device__ __forceinline__ void reduce_and_store(const float* spart, int nteams,
 // cameras in the same order together and each camera's maps are read from
 // HBM about once.
 template <typename FT, typename WT, int NV>
-__global__ void __launch_bounds__(256) fwd_anchor_kernel(const FwdArgs p) {
+__global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anchor_kernel(const FwdArgs p) {
     constexpr int CPL = Elem<FT>::VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nmaps = p.Ncam * p.Nscale;
@@ -157,10 +164,22 @@ __global__ void __launch_bounds__(256) fwd_anchor_kernel(const FwdArgs p) {
     const FwdSmem lay(nmaps, p.P, p.Ncam, nteams, p.C);
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
     float4* sbox = reinterpret_cast<float4*>(smem + lay.box);
+    float* svn = reinterpret_cast<float*>(smem + lay.vn);
     float2* sloc = reinterpret_cast<float2*>(smem + lay.loc);
     float* spart = reinterpret_cast<float*>(smem + lay.part);
 
     const long long ba = blockIdx.x;
+    if (p.vis) {
+        // occlusion-aware fusion (Sec. 3.2, Eq. 2): camera k's weights scale by v_k / sum_j v_j
+        const float* vrow = p.vis + ba * p.Ncam;
+        if (threadIdx.x < 32) {
+            float sum = 0.0f;
+            for (int k = threadIdx.x; k < p.Ncam; k += 32) sum += __ldg(vrow + k);
+            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+            const float inv = sum != 0.0f ? 1.0f / sum : 0.0f;
+            for (int k = threadIdx.x; k < p.Ncam; k += 32) svn[k] = __ldg(vrow + k) * inv;
+        }
+    }
     const int b = (int)(ba / p.A);
     for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
         smap[i] = load_map(p.shape, p.start, i, p.sum_hw, p.status);
@@ -180,12 +199,103 @@ __global__ void __launch_bounds__(256) fwd_anchor_kernel(const FwdArgs p) {
     float2 acc[CPL / 2];
 #pragma unroll
     for (int j = 0; j < CPL / 2; ++j) acc[j] = make_float2(0.0f, 0.0f);
-    accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc);
+    accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc,
+                                  p.vis ? svn : nullptr);
 
     float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
     for (int j = 0; j < CPL / 2; j += 2)
         *reinterpret_cast<float4*>(mine + 2 * j) = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+    __syncthreads();
+    reduce_and_store(spart, nteams, p.C, p.out, p.out_t, ba);
+}
+
+// ---------------------------------------------------------------------------
+// Half2-accumulating forward (the paper's FP16 plugin arithmetic, Sec. 5.3):
+// FP16 features and weights, two channels per instruction, and the weighted
+// sum kept in half2 registers until the anchor's partial rows are written.
+// The teams' partial rows are then added in FP32.  Same mapping, cull and
+// loads as the FP32-accumulating kernel; only the arithmetic differs.
+// ---------------------------------------------------------------------------
+template <int NV>
+__global__ void __launch_bounds__(256) fwd_anchor_h2_kernel(const FwdArgs p) {
+    constexpr int VEC = 8;
+    constexpr int CPL = VEC * NV;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nmaps = p.Ncam * p.Nscale;
+    const int tpw = 32 / p.rt;
+    const int nteams = (blockDim.x >> 5) * tpw;
+    const FwdSmem lay(nmaps, p.P, p.Ncam, nteams, p.C);
+    MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
+    float4* sbox = reinterpret_cast<float4*>(smem + lay.box);
+    float2* sloc = reinterpret_cast<float2*>(smem + lay.loc);
+    float* spart = reinterpret_cast<float*>(smem + lay.part);
+    const long long ba = blockIdx.x;
+    const int b = (int)(ba / p.A);
+    for (int i = threadIdx.x; i < nmaps; i += blockDim.x) smap[i] = load_map(p.shape, p.start, i, p.sum_hw, p.status);
+    const float2* gloc = reinterpret_cast<const float2*>(p.loc) + ba * (long long)(p.P * p.Ncam);
+    for (int i = threadIdx.x; i < p.P * p.Ncam; i += blockDim.x) sloc[i] = __ldg(gloc + i);
+    __syncthreads();
+    for (int k = threadIdx.x; k < p.Ncam; k += blockDim.x) sbox[k] = camera_box(smap + k * p.Nscale, p.Nscale);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int team = (threadIdx.x >> 5) * tpw + lane / p.rt;
+    const int c0 = (lane & (p.rt - 1)) * CPL;
+    const int g = c0 / p.Cg;
+    const __half* fb = reinterpret_cast<const __half*>(p.feat) + (long long)b * p.sum_hw * p.C + c0;
+    const __half* wb = reinterpret_cast<const __half*>(p.w) + ba * ((long long)p.P * p.Ncam * p.Nscale * p.G) + g;
+    __half2 acc[CPL / 2];
+#pragma unroll
+    for (int j = 0; j < CPL / 2; ++j) acc[j] = __float2half2_rn(0.0f);
+    const int nitems = p.Ncam * p.P;
+    for (int item = team; item < nitems; item += nteams) {
+        const int k = item / p.P;
+        const int pp = item - k * p.P;
+        const float2 uv = sloc[pp * p.Ncam + k];
+        if (!in_box(uv, sbox[k])) continue;
+        const __half* wrow = wb + ((long long)pp * p.Ncam + k) * p.Nscale * p.G;
+        const MapInfo* mrow = smap + k * p.Nscale;
+        for (int s = 0; s < p.Nscale; ++s) {
+            const MapInfo m = mrow[s];
+            Cell c;
+            if (m.W == 0 || !locate(uv.x, uv.y, m.H, m.W, c)) continue;
+            const float wv = __half2float(__ldg(wrow + (long long)s * p.G));
+            const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
+            const __half2 w00 = __float2half2_rn(wv * ax * ay), w01 = __float2half2_rn(wv * c.fx * ay);
+            const __half2 w10 = __float2half2_rn(wv * ax * c.fy), w11 = __float2half2_rn(wv * c.fx * c.fy);
+            const bool vx0 = c.x0 >= 0, vx1 = c.x0 + 1 < m.W, vy0 = c.y0 >= 0, vy1 = c.y0 + 1 < m.H;
+            const __half* p00 = fb + (long long)(m.start + c.y0 * m.W + c.x0) * p.C;
+            const __half* p10 = p00 + (long long)m.W * p.C;
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                const uint4 q0 = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
+                const uint4 q1 = (vy0 && vx1) ? ld16(p00 + p.C + n * VEC) : z;
+                const uint4 q2 = (vy1 && vx0) ? ld16(p10 + n * VEC) : z;
+                const uint4 q3 = (vy1 && vx1) ? ld16(p10 + p.C + n * VEC) : z;
+                const __half2* h0 = reinterpret_cast<const __half2*>(&q0);
+                const __half2* h1 = reinterpret_cast<const __half2*>(&q1);
+                const __half2* h2 = reinterpret_cast<const __half2*>(&q2);
+                const __half2* h3 = reinterpret_cast<const __half2*>(&q3);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    __half2 a = acc[n * 4 + j];
+                    a = __hfma2(w00, h0[j], a);
+                    a = __hfma2(w01, h1[j], a);
+                    a = __hfma2(w10, h2[j], a);
+                    a = __hfma2(w11, h3[j], a);
+                    acc[n * 4 + j] = a;
+                }
+            }
+        }
+    }
+    float* mine = spart + (size_t)team * p.C + c0;
+#pragma unroll
+    for (int j = 0; j < CPL / 2; ++j) {
+        const float2 f = __half22float2(acc[j]);
+        mine[2 * j] = f.x;
+        mine[2 * j + 1] = f.y;
+    }
     __syncthreads();
     reduce_and_store(spart, nteams, p.C, p.out, p.out_t, ba);
 }
@@ -340,11 +450,16 @@ static BatchedKernel batched_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
 }
 
 msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int warps,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, const float* vis, bool half_acc) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);
     if (st != MSDA_OK) return st;
     FwdKernel k = fwd_kernel_for(p.feat_t, p.w_t, p.nv);
+    if (half_acc) {
+        if (p.feat_t != MSDA_F16 || p.w_t != MSDA_F16 || vis)
+            return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: half2 accumulation needs FP16 features and weights");
+        k = p.nv == 1 ? fwd_anchor_h2_kernel<1> : p.nv == 2 ? fwd_anchor_h2_kernel<2> : fwd_anchor_h2_kernel<4>;
+    }
     if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: unsupported feature/weight dtype pair");
     const long long nblocks = (long long)p.B * p.A;
     if (nblocks == 0) return MSDA_OK;
@@ -354,7 +469,7 @@ msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int wa
     st = ensure_smem((const void*)k, lay.total, dev);
     if (st != MSDA_OK) return st;
     FwdArgs a;
-    a.feat = p.feat; a.shape = p.shape; a.start = p.start; a.loc = p.loc; a.w = p.w;
+    a.feat = p.feat; a.shape = p.shape; a.start = p.start; a.loc = p.loc; a.w = p.w; a.vis = vis;
     a.out = out; a.out_t = out_t;
     a.B = p.B; a.sum_hw = p.sum_hw; a.C = p.C; a.Ncam = p.Ncam; a.Nscale = p.Nscale;
     a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.status = dev.status;

@@ -50,14 +50,17 @@ bool pick_split_pref(int C, int G, msda_dtype t, int pref, int* nv, int* rt);
 
 int dtype_size(msda_dtype t);
 
-// Kernel launchers (validated inputs).
+// Kernel launchers (validated inputs).  launch_backward_loc_w's `scatter`:
+// 0 = no feature gradient, 1 = clear grad_feat then scatter, 2 = scatter
+// into a grad_feat the caller already cleared.
 msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int warps,
-                           cudaStream_t stream);
+                           cudaStream_t stream, const float* vis = nullptr, bool half_acc = false);
 msda_status launch_backward_atomic(const Problem& p, const float* grad_out, float* grad_feat,
-                                   float* grad_loc, float* grad_w, int warps, cudaStream_t stream);
+                                   float* grad_loc, float* grad_w, void* ws, size_t ws_bytes, int warps,
+                                   bool zeroed, cudaStream_t stream);
 msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float* grad_feat,
                                   float* grad_loc, float* grad_w, int warps, int scatter,
-                                  cudaStream_t stream);
+                                  cudaStream_t stream, unsigned long long* counter = nullptr);
 size_t backward_det_workspace(const Problem& p);
 msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
                                 float* grad_loc, float* grad_w, void* ws, size_t ws_bytes,
@@ -80,6 +83,8 @@ msda_status launch_forward_cg(const Problem& p, void* out, msda_dtype out_t, voi
                               cudaStream_t stream);
 msda_status launch_backward_cg(const Problem& p, const float* grad_out, float* grad_feat, float* grad_loc,
                                float* grad_w, void* ws, size_t ws_bytes, cudaStream_t stream);
+msda_status launch_keypoints(const float* anchors, const float* offsets, const float* dt, const float* proj,
+                             const float* img_wh, float* loc, int B, int A, int P, int Ncam, cudaStream_t stream);
 msda_status launch_probe(const void* buf, size_t bytes, int reps, int blocks, int rows,
                          uint32_t* sink, cudaStream_t stream);
 

@@ -81,9 +81,73 @@ class Problem:
         """The same problem restricted to the anchors ``idx`` (anchors are independent)."""
         idx = torch.as_tensor(idx, dtype=torch.long)
         go = None if self.grad_out is None else self.grad_out[:, idx]
+        meta = dict(self.meta)
+        if meta.get("out_mask") is not None:
+            meta["out_mask"] = meta["out_mask"][:, idx]
         return Problem(self.feat, self.spatial_shape, self.scale_start_index,
                        self.sampling_location[:, idx].contiguous(), self.weights[:, idx].contiguous(),
-                       None if go is None else go.contiguous(), self.name + "[anchors]", dict(self.meta))
+                       None if go is None else go.contiguous(), self.name + "[anchors]", meta)
+
+
+def make_visibility(pr: Problem, seed: int, zero_frac: float = 0.1) -> torch.Tensor:
+    """Visibility scores [B, A, Ncam] for the occlusion-aware fusion: U(0, 1),
+    0 for the (anchor, camera) pairs pushed out of view, and 0 for a further
+    seeded `zero_frac` of pairs (occluded).  Drawn from its own generator so
+    the problem's draws are unchanged."""
+    gen = torch.Generator().manual_seed(10_000 + seed)
+    B, A, _, K, _ = pr.sampling_location.shape
+    v = torch.rand(B, A, K, generator=gen, dtype=torch.float32)
+    v[torch.rand(B, A, K, generator=gen) < zero_frac] = 0.0
+    mask = pr.meta.get("out_mask")
+    if mask is not None:
+        v[mask] = 0.0
+    return v.contiguous()
+
+
+def look_at_camera(eye, target, focal: float, width: int, height: int) -> torch.Tensor:
+    """3x4 world -> homogeneous pixel matrix of a pinhole camera at `eye`
+    looking at `target` (world z up), principal point at the image centre."""
+    eye = torch.as_tensor(eye, dtype=torch.float64)
+    fwd = torch.as_tensor(target, dtype=torch.float64) - eye
+    fwd = fwd / fwd.norm()
+    right = torch.linalg.cross(fwd, torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64))
+    right = right / right.norm()
+    down = torch.linalg.cross(fwd, right)
+    R = torch.stack([right, down, fwd])                  # world -> camera rows
+    t = -R @ eye
+    K = torch.tensor([[focal, 0.0, width / 2.0], [0.0, focal, height / 2.0], [0.0, 0.0, 1.0]], dtype=torch.float64)
+    return K @ torch.cat([R, t[:, None]], dim=1)
+
+
+def make_scene_geometry(seed: int, B: int, A: int, P: int, ncam: int, img=(1920, 1080)):
+    """Synthetic outside-in rig and anchors for the keypoint prologue.
+
+    Cameras sit on a 30 m circle at 6 m height looking at the centre of a
+    40 m x 40 m floor; anchors are boxes on the floor (sizes 0.5..2 m, any
+    yaw, velocity ~ N(0, 1) m/s, dt = 0.1 s); the first 7 keypoints are the
+    box centre and its six face centres at 0.45 box units, the rest are
+    learned-style offsets ~ U[-0.5, 0.5]^3.  Returns anchors [B, A, 11],
+    offsets [B, A, P, 3], dt [B], proj [B, ncam, 3, 4], img_wh [ncam, 2]
+    (float32)."""
+    gen = torch.Generator().manual_seed(20_000 + seed)
+    ctr = torch.rand(B, A, 3, generator=gen) * torch.tensor([40.0, 40.0, 1.0]) - torch.tensor([20.0, 20.0, 0.0])
+    size = torch.rand(B, A, 3, generator=gen) * 1.5 + 0.5
+    yaw = torch.rand(B, A, generator=gen) * 2 * math.pi - math.pi
+    vel = torch.randn(B, A, 3, generator=gen)
+    anchors = torch.cat([ctr, size, torch.sin(yaw)[..., None], torch.cos(yaw)[..., None], vel], dim=-1)
+    fixed = torch.tensor([[0, 0, 0], [0.45, 0, 0], [-0.45, 0, 0], [0, 0.45, 0], [0, -0.45, 0], [0, 0, 0.45],
+                          [0, 0, -0.45]], dtype=torch.float32)[:P]
+    learned = torch.rand(B, A, max(0, P - fixed.shape[0]), 3, generator=gen) - 0.5
+    offsets = torch.cat([fixed.expand(B, A, -1, -1), learned], dim=2)
+    dt = torch.full((B,), 0.1)
+    proj = []
+    for k in range(ncam):
+        ang = 2 * math.pi * k / max(ncam, 1)
+        eye = [30 * math.cos(ang), 30 * math.sin(ang), 6.0]
+        proj.append(look_at_camera(eye, [0.0, 0.0, 0.0], 1000.0, img[0], img[1]))
+    proj = torch.stack(proj).float().expand(B, -1, -1, -1).contiguous()
+    img_wh = torch.tensor([img] * ncam, dtype=torch.float32)
+    return (anchors.float().contiguous(), offsets.float().contiguous(), dt, proj, img_wh)
 
 
 def tables(cam_maps: Sequence[Sequence[Tuple[int, int]]]) -> Tuple[torch.Tensor, torch.Tensor, int]:
@@ -128,7 +192,8 @@ def make_problem(gen: torch.Generator, *, B: int, cam_maps, C: int, G: int, A: i
         loc[..., 0] += 2.0 * out_mask[:, :, None, :].to(loc.dtype)
     go = torch.randn(B, A, C, generator=gen, dtype=torch.float32) if with_grad else None
     meta = dict(out_frac=out_frac, feat_dtype=feat_dtype, w_dtype=w_dtype,
-                n_out_pairs=int(out_mask.sum()), loc_range=loc_range, feat_scale=feat_scale)
+                n_out_pairs=int(out_mask.sum()), loc_range=loc_range, feat_scale=feat_scale,
+                out_mask=out_mask)
     return Problem(feat.contiguous(), shape, start, loc.contiguous(), w, go, name, meta)
 
 

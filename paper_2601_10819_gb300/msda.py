@@ -40,7 +40,11 @@ class MSDAError(RuntimeError):
 
 class msda_tuning(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("variant", ctypes.c_int), ("vectors_per_lane", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("variant", ctypes.c_int), ("vectors_per_lane", ctypes.c_int), ("flags", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
+
+
+FLAG_GRAD_FEAT_ZEROED = 1
 
 
 class msda_scene(ctypes.Structure):
@@ -70,6 +74,10 @@ def load(path: Optional[str] = None):
         lib.msda_forward_workspace_size.restype = sz
         lib.msda_forward.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i] + [i] * 8 + [vp, sz, tp, vp]
         lib.msda_forward.restype = i
+        lib.msda_forward_oae.argtypes = [vp, i, vp, vp, vp, vp, i, vp, vp, i] + [i] * 8 + [tp, vp]
+        lib.msda_forward_oae.restype = i
+        lib.msda_keypoints.argtypes = [vp] * 6 + [i] * 4 + [vp]
+        lib.msda_keypoints.restype = i
         lib.msda_backward_workspace_size.argtypes = [i] * 9
         lib.msda_backward_workspace_size.restype = sz
         lib.msda_backward.argtypes = [vp, i, vp, vp, vp, vp, i, vp, vp, vp, vp] + [i] * 8 + [i, vp, sz, tp, vp]
@@ -100,14 +108,16 @@ def _stream(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
-def _tuning(warps: Optional[int], blocks_per_sm: Optional[int] = None, variant: int = 0, vec: int = 0):
-    if not warps and not blocks_per_sm and not variant and not vec:
+def _tuning(warps: Optional[int], blocks_per_sm: Optional[int] = None, variant: int = 0, vec: int = 0,
+            flags: int = 0):
+    if not warps and not blocks_per_sm and not variant and not vec and not flags:
         return None
     t = msda_tuning()
     t.warps_per_block = int(warps or 0)
     t.blocks_per_sm = int(blocks_per_sm or 0)
     t.variant = int(variant)
     t.vectors_per_lane = int(vec or 0)
+    t.flags = int(flags)
     return ctypes.byref(t)
 
 
@@ -175,14 +185,57 @@ def forward(feat, spatial_shape, scale_start_index, sampling_location, weights, 
     return out
 
 
+def forward_oae(feat, spatial_shape, scale_start_index, sampling_location, weights, visibility, *,
+                out: Optional[torch.Tensor] = None, out_dtype: torch.dtype = torch.float32,
+                warps: Optional[int] = None, vec: int = 0) -> torch.Tensor:
+    """msda_forward_oae: the operator fused with the visibility-weighted mean over cameras."""
+    lib = load()
+    B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
+    if visibility.dtype != torch.float32 or not visibility.is_cuda or not visibility.is_contiguous() or \
+            tuple(visibility.shape) != (B, A, Ncam):
+        raise ValueError("visibility must be a contiguous float32 CUDA tensor [B, A, Ncam]")
+    if out is None:
+        out = torch.empty(B, A, C, dtype=out_dtype, device=feat.device)
+    rc = lib.msda_forward_oae(_ptr(feat), _DT[feat.dtype], _ptr(spatial_shape), _ptr(scale_start_index),
+                              _ptr(sampling_location), _ptr(weights), _DT[weights.dtype], _ptr(visibility),
+                              _ptr(out), _DT[out.dtype], B, sum_hw, C, Ncam, Nscale, A, P, G,
+                              _tuning(warps, None, 0, vec), ctypes.c_void_p(_stream(feat.device)))
+    _check("msda_forward_oae", rc)
+    return out
+
+
+def keypoints(anchors, offsets, dt, proj, img_wh, *, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """msda_keypoints: sampling_location [B, A, P, Ncam, 2] from anchors and cameras."""
+    lib = load()
+    for name, t in (("anchors", anchors), ("offsets", offsets), ("dt", dt), ("proj", proj), ("img_wh", img_wh)):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    B, A, _ = anchors.shape
+    P = offsets.shape[2]
+    Ncam = proj.shape[1]
+    if anchors.shape[2] != 11 or tuple(offsets.shape) != (B, A, P, 3) or tuple(dt.shape) != (B,) or \
+            tuple(proj.shape) != (B, Ncam, 3, 4) or tuple(img_wh.shape) != (Ncam, 2):
+        raise ValueError("bad keypoint prologue shapes")
+    if out is None:
+        out = torch.empty(B, A, P, Ncam, 2, dtype=torch.float32, device=anchors.device)
+    rc = lib.msda_keypoints(_ptr(anchors), _ptr(offsets), _ptr(dt), _ptr(proj), _ptr(img_wh), _ptr(out),
+                            B, A, P, Ncam, ctypes.c_void_p(_stream(anchors.device)))
+    _check("msda_keypoints", rc)
+    return out
+
+
 def backward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G, deterministic: bool) -> int:
     return int(load().msda_backward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G, int(bool(deterministic))))
 
 
 def backward(feat, spatial_shape, scale_start_index, sampling_location, weights, grad_out, *,
              deterministic: bool = False, workspace: Optional[torch.Tensor] = None,
-             grads=None, warps: Optional[int] = None, variant: int = 0, vec: int = 0):
-    """msda_backward: (grad_feat, grad_loc, grad_weights), all float32."""
+             grads=None, warps: Optional[int] = None, variant: int = 0, vec: int = 0,
+             grad_feat_zeroed: bool = False):
+    """msda_backward: (grad_feat, grad_loc, grad_weights), all float32.
+
+    grad_feat_zeroed: the caller already cleared grads[0] (atomic mode only).
+    """
     lib = load()
     B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
     if grad_out.dtype != torch.float32 or not grad_out.is_contiguous() or tuple(grad_out.shape) != (B, A, C):
@@ -201,7 +254,8 @@ def backward(feat, spatial_shape, scale_start_index, sampling_location, weights,
     rc = lib.msda_backward(_ptr(feat), _DT[feat.dtype], _ptr(spatial_shape), _ptr(scale_start_index),
                            _ptr(sampling_location), _ptr(weights), _DT[weights.dtype], _ptr(grad_out),
                            _ptr(gf), _ptr(gl), _ptr(gw), B, sum_hw, C, Ncam, Nscale, A, P, G,
-                           int(bool(deterministic)), _ptr(workspace), ws_bytes, _tuning(warps, None, variant, vec),
+                           int(bool(deterministic)), _ptr(workspace), ws_bytes,
+                           _tuning(warps, None, variant, vec, FLAG_GRAD_FEAT_ZEROED if grad_feat_zeroed else 0),
                            ctypes.c_void_p(_stream(dev)))
     _check("msda_backward", rc)
     return gf, gl, gw

@@ -148,3 +148,38 @@ def tune_batched(scenes, force: bool = False) -> Dict:
         plans[key].run()
 
     return _best("batched", sig, BATCHED_CANDIDATES, run, force)
+
+
+def main():
+    """Search the benchmark workloads on this GPU and write a tuning table."""
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=SHIPPED)
+    args = ap.parse_args()
+    from . import inputs
+    os.environ["MSDA_TUNE_CACHE"] = args.out + ".search.json"
+    dev = torch.device("cuda")
+    pr = inputs.make_workload(2).to(dev)
+    T = pr.tensors()
+    B, sum_hw, C = pr.feat.shape
+    _, A, P, K, _ = pr.sampling_location.shape
+    S, G = pr.weights.shape[4:]
+    out = torch.empty(B, A, C, device=dev)
+    fws = torch.empty(msda.forward_workspace_size(B, sum_hw, C, K, S, A, P, G), dtype=torch.uint8, device=dev)
+    grads = (torch.zeros(B, sum_hw, C, device=dev), torch.empty(B, A, P, K, 2, device=dev),
+             torch.empty(B, A, P, K, S, G, device=dev))
+    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    tune_forward(T, out, workspace=fws, force=True)
+    tune_backward(T, pr.grad_out, grads, workspace=ws, force=True)
+    scenes = [s.to(dev) for s in inputs.make_workload(4, with_grad=False)]
+    tune_batched(scenes, force=True)
+    with open(os.environ["MSDA_TUNE_CACHE"]) as f:
+        found = json.load(f)
+    table = {k: {"best": v["best"], "ms": round(v["ms"], 4)} for k, v in found.items()}
+    with open(args.out, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    print(json.dumps(table, indent=1))
+
+
+if __name__ == "__main__":
+    main()

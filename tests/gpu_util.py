@@ -34,7 +34,7 @@ def to_dev(pr, device="cuda"):
     return pr.to(device)
 
 
-def gpu_forward(pr, **kw):
+def gpu_forward(pr, **kw):  # kw: out_dtype, workspace, warps, variant, vec
     d = pr.to("cuda")
     out = msda.forward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights, **kw)
     torch.cuda.synchronize()

@@ -98,7 +98,7 @@ def test_batched_validation(lib):
 
 def test_workspace_sizes(lib):
     assert lib.msda_forward_workspace_size(2, 100, 32, 3, 2, 5, 4, 4) >= 2 * 3 * 5 * 32 * 4
-    assert lib.msda_backward_workspace_size(1, 100, 32, 2, 2, 4, 3, 4, 0) == 0
+    assert lib.msda_backward_workspace_size(1, 100, 32, 2, 2, 4, 3, 4, 0) == 256  # atomic mode: work counter
     n = 1 * 4 * 3 * 2 * 2
     ws = lib.msda_backward_workspace_size(1, 100, 32, 2, 2, 4, 3, 4, 1)
     assert ws >= 4 * 4 * n * 4 + 4 * 101  # keys, values (double-buffered) and row offsets

@@ -184,3 +184,19 @@ def test_uncovered_rows_are_zero_and_overlaps_reported():
     g = gpu_backward(ov, True)  # the radix form handles overlapping maps
     check_against_oracle(ov, g, TOL_FP32, "overlapping maps, radix form")
     assert msda.device_status() == 0
+
+
+def test_caller_zeroed_flag_accumulates_into_grad_feat():
+    pr = inputs.make_workload(0)
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    ref = msda.backward(*T, d.grad_out)
+    gf = torch.zeros_like(ref[0])
+    got = msda.backward(*T, d.grad_out, grads=(gf, torch.empty_like(ref[1]), torch.empty_like(ref[2])),
+                        grad_feat_zeroed=True)
+    assert relerr(got[0].cpu().double().numpy(), ref[0].cpu().double().numpy()) <= 1e-6
+    assert torch.equal(got[1], ref[1]) and torch.equal(got[2], ref[2])
+    ones = torch.ones_like(ref[0])
+    got = msda.backward(*T, d.grad_out, grads=(ones, torch.empty_like(ref[1]), torch.empty_like(ref[2])),
+                        grad_feat_zeroed=True)
+    assert relerr(got[0].cpu().double().numpy() - 1.0, ref[0].cpu().double().numpy()) <= 1e-6
