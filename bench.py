@@ -57,9 +57,14 @@ def parse():
     ap.add_argument("--cpu-sample-anchors", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deterministic", action="store_true", help="time the deterministic backward instead")
+    ap.add_argument("--clear", default="side", choices=["side", "inline"],
+                    help="atomic backward: clear the feature gradient on a side stream during the forward (side) "
+                         "or with a memset inside msda_backward (inline)")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in launch mappings")
     ap.add_argument("--extras", action="store_true",
                     help="also time the fused occlusion-aware forward, the keypoint prologue and the half2 forward")
+    ap.add_argument("--configs", action="store_true",
+                    help="also time the 6-camera (FP32, BF16) and 16-camera training workloads")
     ap.add_argument("--with-batched", action="store_true",
                     help="also time the 16-scene batched serving workload (per-scene p50/p99)")
     return ap.parse_args()
@@ -267,6 +272,52 @@ def extras(pr, dev, ft, reps=20):
     }
 
 
+def other_configs(dev, l2_gbs, hbm_peak, reps=20):
+    """Forward and atomic backward timings of the non-headline workloads, each with its gather roofline.
+
+    A frame is one batch element; a backward timing includes clearing the feature gradient.
+    """
+    from paper_2601_10819_gb300 import inputs, msda, roofline
+    res = {}
+    for name, idx, fdt, wdt in (("sparse4d-6cam-fp32", 1, "f32", "f32"), ("sparse4d-6cam-bf16", 1, "bf16", "bf16"),
+                                ("train-16cam-b4", 3, None, None)):
+        pr = inputs.make_workload(idx, feat_dtype=fdt, w_dtype=wdt)
+        cnt = roofline.count(pr)
+        d = pr.to(dev)
+        T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+        B, sum_hw, C = d.feat.shape
+        out = torch.empty(d.grad_out.shape, device=dev)
+        grads = (torch.empty(B, sum_hw, C, device=dev), torch.empty(d.sampling_location.shape, device=dev),
+                 torch.empty(d.weights.shape, device=dev))
+        ws = torch.empty(msda.backward_workspace_size(B, sum_hw, C, *d.weights.shape[3:5], d.weights.shape[1],
+                                                      d.weights.shape[2], d.weights.shape[5], False),
+                         dtype=torch.uint8, device=dev)
+
+        def tm(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / reps * 1e3
+
+        f_us = tm(lambda: msda.forward(*T, out=out))
+        f_staged_us = tm(lambda: msda.forward(*T, out=out, workspace="auto"))
+        b_us = tm(lambda: msda.backward(*T, d.grad_out, workspace=ws, grads=grads))
+        roof_f = max(cnt.fwd_hbm_bytes / (hbm_peak * 1e9), cnt.fwd_l2_gather_bytes / (l2_gbs * 1e9)) * 1e6
+        roof_b = max(cnt.bwd_hbm_bytes / (hbm_peak * 1e9), cnt.bwd_l2_bytes / (l2_gbs * 1e9)) * 1e6
+        res[name] = {"frames": B, "fwd_us_per_frame": f_us / B, "fwd_staged_us_per_frame": f_staged_us / B,
+                     "bwd_us_per_frame": b_us / B,
+                     "fwd_gsamples_per_s": cnt.nominal_samples / (f_us * 1e-6) / 1e9,
+                     "fwd_gather_roof_frac": roof_f / f_us, "bwd_gather_roof_frac": roof_b / b_us}
+        del d, out, grads
+    return res
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle, timed on the host cores."""
     if rank != 0:
@@ -352,21 +403,22 @@ def main():
         ft = tune.tune_forward(tensors, out, workspace=fws)
         bt = tune.tune_backward(tensors, d.grad_out, (gf, gl, gw), deterministic=det, workspace=ws)
     fwd_ws = fws if ft["workspace"] else None
-    side = torch.cuda.Stream(dev)  # clears the feature gradient while the forward runs (atomic mode)
+    side_clear = not det and args.clear != "inline"
+    side = torch.cuda.Stream(dev)  # clears the feature gradient while the forward runs
     main = torch.cuda.current_stream(dev)
 
     def fwd(tens=None):
-        if not det:
+        if side_clear:
             side.wait_stream(main)  # the previous backward is done with grad_feat
             with torch.cuda.stream(side):
                 gf.zero_()
         msda.forward(*(tens or tensors), out=out, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
 
     def bwd(tens=None, go=None):
-        if not det:
+        if side_clear:
             main.wait_stream(side)
         msda.backward(*(tens or tensors), d.grad_out if go is None else go, deterministic=det, workspace=ws,
-                      grads=(gf, gl, gw), warps=bt["warps"] or None, vec=bt["vec"], grad_feat_zeroed=not det)
+                      grads=(gf, gl, gw), warps=bt["warps"] or None, vec=bt["vec"], grad_feat_zeroed=side_clear)
 
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -465,7 +517,9 @@ def main():
         "vs_baseline": None, "dtype": "bf16", "accumulate": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": B, "parallelism": f"replicas x{world}",
                    "backward": "deterministic" if det else "atomic",
-                   "overlap": None if det else "feature gradient cleared on a side stream during the forward",
+                   "grad_feat_clear": None if det else {
+                       "side": "torch fill on a side stream during the forward",
+                       "inline": "memset inside msda_backward"}[args.clear],
                    "l2": "inputs larger than L2 (feat 355 MB, grad_feat 710 MB per frame); no flush"},
         "gsamples_per_s": cnt.nominal_samples * frames / (ms_per_step * 1e-3) / 1e9,
         "inview_gsamples_per_s": cnt.inview_samples * frames / (ms_per_step * 1e-3) / 1e9,
@@ -490,6 +544,8 @@ def main():
         line["batched_serving"] = batched_serving(dev, stream, tune_it=not args.no_tune)
     if args.extras:
         line["extras"] = extras(pr, dev, ft)
+    if args.configs:
+        line["other_workloads"] = other_configs(dev, l2_gather_gbs, hbm_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, args.cpu_sample_anchors)
     if rank == 0:

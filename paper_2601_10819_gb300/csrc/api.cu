@@ -1,7 +1,7 @@
 // C-ABI entry points of libmsda_gb300: argument validation, per-device
 // constants, the device status word and error messages.  Every compute step
-// is a kernel of fwd.cu, bwd.cu, det.cu or probe.cu; nothing here touches
-// tensor data.
+// is a kernel of fwd.cu, bwd.cu, det.cu, cg.cu, prologue.cu or probe.cu;
+// nothing here touches tensor data.
 #include <stdarg.h>
 #include <stdio.h>
 

@@ -44,8 +44,12 @@ struct BwdArgs {
 
 constexpr int kItemsPerGrab = 4;  // items per team taken from the counter at once
 
-__device__ __forceinline__ float4 scale4(float a, const float4& v) {
-    return make_float4(a * v.x, a * v.y, a * v.z, a * v.w);
+// addr[0..3] += a * v as one 16-byte FP32 vector reduction in global memory with no return value
+// (red.global.add.v4.f32, sm_90 and later).  Written out because atomicAdd(float4*) may be compiled as a
+// generic-space atomic that returns the old values, which doubles the L2<->SM traffic of the scatter.
+__device__ __forceinline__ void red_add_v4(float* addr, float a, const float4& v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(__cvta_generic_to_global(addr)), "f"(a * v.x), "f"(a * v.y), "f"(a * v.z), "f"(a * v.w));
 }
 
 __device__ __forceinline__ float team_sum(float v, unsigned mask, int width) {
@@ -178,10 +182,10 @@ __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
                         const float c00 = wj * o00, c01 = wj * o01, c10 = wj * o10, c11 = wj * o11;
                         const float4 gv = __ldg(reinterpret_cast<const float4*>(gorow + ci + j * cstride));
                         float* qq = g00 + j * cstride;
-                        if (vy0 && vx0) atomicAdd(reinterpret_cast<float4*>(qq), scale4(c00, gv));
-                        if (vy0 && vx1) atomicAdd(reinterpret_cast<float4*>(qq + p.C), scale4(c01, gv));
-                        if (vy1 && vx0) atomicAdd(reinterpret_cast<float4*>(qq + rW), scale4(c10, gv));
-                        if (vy1 && vx1) atomicAdd(reinterpret_cast<float4*>(qq + rW + p.C), scale4(c11, gv));
+                        if (vy0 && vx0) red_add_v4(qq, c00, gv);
+                        if (vy0 && vx1) red_add_v4(qq + p.C, c01, gv);
+                        if (vy1 && vx0) red_add_v4(qq + rW, c10, gv);
+                        if (vy1 && vx1) red_add_v4(qq + rW + p.C, c11, gv);
                     }
                 }
             }

@@ -160,12 +160,13 @@ AUTO = "auto"
 
 def forward(feat, spatial_shape, scale_start_index, sampling_location, weights, *,
             out: Optional[torch.Tensor] = None, out_dtype: torch.dtype = torch.float32,
-            workspace=AUTO, warps: Optional[int] = None, variant: int = 0, vec: int = 0) -> torch.Tensor:
+            workspace=None, warps: Optional[int] = None, variant: int = 0, vec: int = 0) -> torch.Tensor:
     """msda_forward: out[B, A, C] on the current stream of feat's device.
 
-    workspace: "auto" (a buffer from torch's allocator, which enables the
-    staged camera-group kernels), a uint8 CUDA tensor, or None (the
-    anchor-per-block kernel, no scratch).
+    workspace: None (default: the anchor-per-block kernel, no scratch, the
+    faster form on the measured workloads), "auto" (a buffer from torch's
+    allocator, which selects the staged camera-group kernels) or a uint8
+    CUDA tensor (likewise).
     """
     lib = load()
     B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
@@ -231,10 +232,14 @@ def backward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G, deterministic: 
 def backward(feat, spatial_shape, scale_start_index, sampling_location, weights, grad_out, *,
              deterministic: bool = False, workspace: Optional[torch.Tensor] = None,
              grads=None, warps: Optional[int] = None, variant: int = 0, vec: int = 0,
-             grad_feat_zeroed: bool = False):
+             grad_feat_zeroed: bool = False, flags: int = 0):
     """msda_backward: (grad_feat, grad_loc, grad_weights), all float32.
 
     grad_feat_zeroed: the caller already cleared grads[0] (atomic mode only).
+    workspace: allocated when None (or, in deterministic mode, too small).  In
+    atomic mode a caller's workspace is passed through as is: one of fewer
+    than 8 bytes selects the static-stride item order.
+    flags: extra MSDA_FLAG_* bits.
     """
     lib = load()
     B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
@@ -248,14 +253,16 @@ def backward(feat, spatial_shape, scale_start_index, sampling_location, weights,
     else:
         gf, gl, gw = grads
     need = backward_workspace_size(B, sum_hw, C, Ncam, Nscale, A, P, G, deterministic)
-    if need and (workspace is None or workspace.numel() * workspace.element_size() < need):
+    small = workspace is not None and workspace.numel() * workspace.element_size() < need
+    if need and (workspace is None or (small and deterministic)):
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     rc = lib.msda_backward(_ptr(feat), _DT[feat.dtype], _ptr(spatial_shape), _ptr(scale_start_index),
                            _ptr(sampling_location), _ptr(weights), _DT[weights.dtype], _ptr(grad_out),
                            _ptr(gf), _ptr(gl), _ptr(gw), B, sum_hw, C, Ncam, Nscale, A, P, G,
                            int(bool(deterministic)), _ptr(workspace), ws_bytes,
-                           _tuning(warps, None, variant, vec, FLAG_GRAD_FEAT_ZEROED if grad_feat_zeroed else 0),
+                           _tuning(warps, None, variant, vec,
+                                   (FLAG_GRAD_FEAT_ZEROED if grad_feat_zeroed else 0) | int(flags)),
                            ctypes.c_void_p(_stream(dev)))
     _check("msda_backward", rc)
     return gf, gl, gw

@@ -168,7 +168,7 @@ def main():
     fws = torch.empty(msda.forward_workspace_size(B, sum_hw, C, K, S, A, P, G), dtype=torch.uint8, device=dev)
     grads = (torch.zeros(B, sum_hw, C, device=dev), torch.empty(B, A, P, K, 2, device=dev),
              torch.empty(B, A, P, K, S, G, device=dev))
-    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    ws = torch.empty(msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, False), dtype=torch.uint8, device=dev)
     tune_forward(T, out, workspace=fws, force=True)
     tune_backward(T, pr.grad_out, grads, workspace=ws, force=True)
     scenes = [s.to(dev) for s in inputs.make_workload(4, with_grad=False)]

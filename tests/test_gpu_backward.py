@@ -200,3 +200,102 @@ def test_caller_zeroed_flag_accumulates_into_grad_feat():
     got = msda.backward(*T, d.grad_out, grads=(ones, torch.empty_like(ref[1]), torch.empty_like(ref[2])),
                         grad_feat_zeroed=True)
     assert relerr(got[0].cpu().double().numpy() - 1.0, ref[0].cpu().double().numpy()) <= 1e-6
+
+
+def _relayout(pr, layout, gen):
+    """The same maps with another row layout: scale-major, padded with uncovered rows, or overlapping."""
+    shape, start = pr.spatial_shape, pr.scale_start_index.clone()
+    ncam, nscale = start.shape
+    sizes = (shape[..., 0] * shape[..., 1]).long()
+    feat = pr.feat
+    if layout == "scale-major":
+        pos = 0
+        for s in range(nscale):
+            for k in range(ncam):
+                start[k, s] = pos
+                pos += int(sizes[k, s])
+    elif layout == "padded":
+        pos = 5  # uncovered rows before, between and after the maps
+        for k in range(ncam):
+            for s in range(nscale):
+                start[k, s] = pos
+                pos += int(sizes[k, s]) + 3
+        B, _, C = feat.shape
+        feat = torch.randn(B, pos + 7, C, generator=gen).to(feat.dtype)
+    elif layout == "overlapping":
+        start[ncam - 1, 0] = 0  # the last camera's finest map reuses the first camera's rows
+    elif layout != "camera-major":
+        raise ValueError(layout)
+    return inputs.Problem(feat.contiguous(), shape, start, pr.sampling_location, pr.weights, pr.grad_out)
+
+
+@pytest.mark.parametrize("layout", ["camera-major", "scale-major", "padded", "overlapping"])
+def test_atomic_item_orders_over_row_layouts(layout):
+    """The atomic backward's ordered hand-out (a work counter in the workspace) and static stride (no
+    workspace) over row layouts that do not follow the camera order, against the oracle; the output
+    buffers start out as NaN, so every element must be written (uncovered rows as zero)."""
+    gen = torch.Generator().manual_seed(11)
+    maps = [[(9, 13), (5, 7), (3, 4)], [(8, 8), (4, 4), (2, 2)], [(12, 5), (6, 3), (3, 2)]]
+    pr = _relayout(inputs.make_problem(gen, B=3, cam_maps=maps, C=64, G=4, A=37, P=5, loc_range=(-0.1, 1.1)),
+                   layout, gen)
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    B, sum_hw, C = d.feat.shape
+    msda.device_status()
+    res = {}
+    for name, ws_bytes in (("ordered", 256), ("static", 0)):
+        grads = tuple(torch.full(s, float("nan"), device="cuda")
+                      for s in ((B, sum_hw, C), d.sampling_location.shape, d.weights.shape))
+        ws = torch.full((ws_bytes,), 0xAB, dtype=torch.uint8, device="cuda")
+        for _ in range(2):  # the second call starts from the first one's counter and gradients
+            g = msda.backward(*T, d.grad_out, workspace=ws, grads=grads, warps=2)
+        torch.cuda.synchronize()
+        res[name] = [t.cpu() for t in g]
+        assert not any(torch.isnan(t).any() for t in res[name])
+        check_against_oracle(pr, res[name], TOL_FP32, f"{name} order, layout {layout}")
+    assert msda.device_status() == 0
+    assert torch.equal(res["ordered"][1], res["static"][1]) and torch.equal(res["ordered"][2], res["static"][2])
+    if layout == "padded":
+        covered = torch.zeros(sum_hw, dtype=torch.bool)
+        for k in range(3):
+            for s in range(3):
+                st = int(pr.scale_start_index[k, s])
+                covered[st:st + int(pr.spatial_shape[k, s, 0] * pr.spatial_shape[k, s, 1])] = True
+        assert torch.all(res["ordered"][0][:, ~covered] == 0)
+
+
+def test_atomic_orders_and_splits_agree_on_training_shape():
+    """Every warp count and vector split of the ordered hand-out on the 16-camera training shape (4 batch
+    elements), against the static stride."""
+    pr = inputs.make_workload(3, ncam=16, batch=4, feat_dtype="bf16", w_dtype="f32")
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    ref = msda.backward(*T, d.grad_out, workspace=torch.empty(0, dtype=torch.uint8, device="cuda"))
+    for warps in (1, 2, 4, 8):
+        for vec in (1, 2, 4):
+            g = msda.backward(*T, d.grad_out, warps=warps, vec=vec)
+            e = relerr(g[0].cpu().double().numpy(), ref[0].cpu().double().numpy())
+            assert e <= 1e-5, (warps, vec, e)
+    assert msda.device_status() == 0
+
+
+def test_side_stream_clear_then_zeroed_backward():
+    """The training-step pattern: grad_feat cleared on a side stream while the forward runs, then the atomic
+    backward with MSDA_FLAG_GRAD_FEAT_ZEROED; equal to a backward that clears by itself."""
+    pr = inputs.make_workload(1, feat_dtype="bf16", w_dtype="bf16").anchors(range(200))
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    ref = [t.cpu() for t in msda.backward(*T, d.grad_out)]
+    B, sum_hw, C = d.feat.shape
+    gf = torch.full((B, sum_hw, C), float("nan"), device="cuda")
+    gl, gw = torch.empty(d.sampling_location.shape, device="cuda"), torch.empty(d.weights.shape, device="cuda")
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        gf.zero_()
+    msda.forward(*T)
+    main.wait_stream(side)
+    g = [t.cpu() for t in msda.backward(*T, d.grad_out, grads=(gf, gl, gw), grad_feat_zeroed=True)]
+    assert relerr(g[0].double().numpy(), ref[0].double().numpy()) <= 1e-6
+    assert torch.equal(g[1], ref[1]) and torch.equal(g[2], ref[2])
+    assert msda.device_status() == 0
