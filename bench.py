@@ -57,9 +57,10 @@ def parse():
     ap.add_argument("--cpu-sample-anchors", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deterministic", action="store_true", help="time the deterministic backward instead")
-    ap.add_argument("--clear", default="side", choices=["side", "inline"],
-                    help="atomic backward: clear the feature gradient on a side stream during the forward (side) "
-                         "or with a memset inside msda_backward (inline)")
+    ap.add_argument("--clear", default="forward", choices=["forward", "side", "inline"],
+                    help="atomic backward: clear the feature gradient inside the forward kernel "
+                         "(msda_forward_train), on a side stream during the forward (side), or with a memset "
+                         "inside msda_backward (inline)")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in launch mappings")
     ap.add_argument("--extras", action="store_true",
                     help="also time the fused occlusion-aware forward, the keypoint prologue and the half2 forward")
@@ -179,6 +180,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def l2_rates(dev, stream, tries=5):
+    """L2 rates measured live (best of `tries` runs of ~0.3 ms each, 64 MB L2-resident buffers): random
+    512-byte row gathers (the operator's corner loads) and random 1 KB FP32 vector reductions (the atomic
+    backward's scatter), in GB/s."""
+    from paper_2601_10819_gb300 import msda
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, reps, rows = nsm * 4, 16, 64
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def best(fn, nbytes):
+        fn()
+        rate = 0.0
+        for _ in range(tries):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            rate = max(rate, nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        return rate
+
+    buf = torch.empty(64 << 20, dtype=torch.uint8, device=dev).random_()
+    gather = best(lambda: msda.probe_read(buf, reps, blocks, rows), blocks * 16 * reps * rows * 512)
+    del buf
+    red_buf = torch.zeros(16 << 20, dtype=torch.float32, device=dev)
+    red = best(lambda: msda.probe_reduce(red_buf, reps // 4, blocks, rows), blocks * 16 * (reps // 4) * rows * 1024)
+    del red_buf
+    return gather, red
+
+
 def cpu_baseline(pr, sample_anchors):
     """The FP64 oracle (as it stands) on the first `sample_anchors` anchors of the frame."""
     import oracle
@@ -272,8 +302,9 @@ def extras(pr, dev, ft, reps=20):
     }
 
 
-def other_configs(dev, l2_gbs, hbm_peak, reps=20):
-    """Forward and atomic backward timings of the non-headline workloads, each with its gather roofline.
+def other_configs(dev, l2_gbs, l2_red_gbs, hbm_peak, reps=20):
+    """Forward and atomic backward timings of the non-headline workloads, each with its roofline: the
+    forward against max(HBM, L2 gathers), the backward against max(HBM, L2 gathers, L2 FP32 reductions).
 
     A frame is one batch element; a backward timing includes clearing the feature gradient.
     """
@@ -309,7 +340,8 @@ def other_configs(dev, l2_gbs, hbm_peak, reps=20):
         f_staged_us = tm(lambda: msda.forward(*T, out=out, workspace="auto"))
         b_us = tm(lambda: msda.backward(*T, d.grad_out, workspace=ws, grads=grads))
         roof_f = max(cnt.fwd_hbm_bytes / (hbm_peak * 1e9), cnt.fwd_l2_gather_bytes / (l2_gbs * 1e9)) * 1e6
-        roof_b = max(cnt.bwd_hbm_bytes / (hbm_peak * 1e9), cnt.bwd_l2_bytes / (l2_gbs * 1e9)) * 1e6
+        roof_b = max(cnt.bwd_hbm_bytes / (hbm_peak * 1e9), cnt.fwd_l2_gather_bytes / (l2_gbs * 1e9),
+                     (cnt.bwd_l2_bytes - cnt.fwd_l2_gather_bytes) / (l2_red_gbs * 1e9)) * 1e6
         res[name] = {"frames": B, "fwd_us_per_frame": f_us / B, "fwd_staged_us_per_frame": f_staged_us / B,
                      "bwd_us_per_frame": b_us / B,
                      "fwd_gsamples_per_s": cnt.nominal_samples / (f_us * 1e-6) / 1e9,
@@ -403,22 +435,28 @@ def main():
         ft = tune.tune_forward(tensors, out, workspace=fws)
         bt = tune.tune_backward(tensors, d.grad_out, (gf, gl, gw), deterministic=det, workspace=ws)
     fwd_ws = fws if ft["workspace"] else None
-    side_clear = not det and args.clear != "inline"
-    side = torch.cuda.Stream(dev)  # clears the feature gradient while the forward runs
+    side_clear = not det and args.clear == "side"
+    fwd_clear = not det and args.clear == "forward"
+    side = torch.cuda.Stream(dev)  # clears the feature gradient while the forward runs (--clear side)
     main = torch.cuda.current_stream(dev)
 
-    def fwd(tens=None):
+    def fwd(tens=None, outs=None):
+        o, g = (out, gf) if outs is None else (outs[0], outs[1])
         if side_clear:
             side.wait_stream(main)  # the previous backward is done with grad_feat
             with torch.cuda.stream(side):
-                gf.zero_()
-        msda.forward(*(tens or tensors), out=out, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
+                g.zero_()
+        if fwd_clear:
+            msda.forward_train(*(tens or tensors), g, out=o, warps=ft["warps"] or None, vec=ft["vec"])
+        else:
+            msda.forward(*(tens or tensors), out=o, workspace=fwd_ws, warps=ft["warps"] or None, vec=ft["vec"])
 
-    def bwd(tens=None, go=None):
+    def bwd(tens=None, go=None, outs=None):
         if side_clear:
             main.wait_stream(side)
         msda.backward(*(tens or tensors), d.grad_out if go is None else go, deterministic=det, workspace=ws,
-                      grads=(gf, gl, gw), warps=bt["warps"] or None, vec=bt["vec"], grad_feat_zeroed=side_clear)
+                      grads=(gf, gl, gw) if outs is None else tuple(outs[1:]), warps=bt["warps"] or None,
+                      vec=bt["vec"], grad_feat_zeroed=side_clear or fwd_clear)
 
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -428,18 +466,7 @@ def main():
     if msda.device_status() != 0:
         raise RuntimeError("device status set during warm-up")
 
-    # L2 read-bandwidth probe (random 512-byte rows from a 64 MB buffer, L2-resident)
-    probe_buf = torch.empty(64 << 20, dtype=torch.uint8, device=dev).random_()
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    blocks, reps, rows = nsm * 4, 4, 64
-    msda.probe_read(probe_buf, reps, blocks, rows)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    msda.probe_read(probe_buf, reps, blocks, rows)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    l2_gather_gbs = blocks * 16 * reps * rows * 512 / (e0.elapsed_time(e1) * 1e-3) / 1e9
-    del probe_buf
+    l2_gather_gbs, l2_red_gbs = l2_rates(dev, stream)
 
     # timed region: exactly K steps, per-call events on the launching stream
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -468,31 +495,51 @@ def main():
     if msda.device_status() != 0:
         raise RuntimeError("device status set during the timed region")
 
-    # end to end through the public API with host buffers (pinned), H2D + compute + D2H each step
+    # End to end through the public API with host buffers (pinned): every step copies its inputs host->device,
+    # runs the forward and backward, and copies out and the three gradients device->host.  Consecutive steps
+    # overlap on three streams (copy-in, compute, copy-out) with two buffer sets, as an input pipeline would.
     h_in = [x.cpu().pin_memory() for x in (pr.feat, pr.sampling_location, pr.weights, pr.grad_out)]
-    h_out = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in (out, gf, gl, gw)]
-    d_in = [torch.empty_like(x, device=dev) for x in h_in]
     h2d = sum(x.numel() * x.element_size() for x in h_in)
-    d2h = sum(x.numel() * x.element_size() for x in h_out)
+    slots = []
+    for _ in range(2):
+        d_in = [torch.empty_like(x, device=dev) for x in h_in]
+        d_out = [torch.empty_like(x) for x in (out, gf, gl, gw)]
+        slots.append((d_in, d_out, [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in d_out]))
+    d2h = sum(x.numel() * x.element_size() for x in slots[0][2])
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev_in, ev_comp, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
 
-    def e2e_step():
-        for h, dd in zip(h_in, d_in):
-            dd.copy_(h, non_blocking=True)
+    def e2e_step(i):
+        j = i % 2
+        d_in, d_out, h_out = slots[j]
+        s_in.wait_event(ev_comp[j])  # the compute that last read this slot's inputs is done
+        with torch.cuda.stream(s_in):
+            for h, dd in zip(h_in, d_in):
+                dd.copy_(h, non_blocking=True)
+        ev_in[j].record(s_in)
+        main.wait_event(ev_in[j])
+        main.wait_event(ev_out[j])   # this slot's outputs have been copied out
         tens = (d_in[0], d.spatial_shape, d.scale_start_index, d_in[1], d_in[2])
-        fwd(tens)
-        bwd(tens, d_in[3])
-        for h, dd in zip(h_out, (out, gf, gl, gw)):
-            h.copy_(dd, non_blocking=True)
+        fwd(tens, d_out)
+        bwd(tens, d_in[3], d_out)
+        ev_comp[j].record(main)
+        s_out.wait_event(ev_comp[j])
+        with torch.cuda.stream(s_out):
+            for h, dd in zip(h_out, d_out):
+                h.copy_(dd, non_blocking=True)
+        ev_out[j].record(s_out)
 
-    e2e_step()
+    for i in range(2):
+        e2e_step(i)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(args.e2e_steps):
-        e2e_step()
-    s1.record(stream)
+    s0.record(main)
+    for i in range(args.e2e_steps):
+        e2e_step(i)
+    main.wait_stream(s_out)
+    s1.record(main)
     torch.cuda.synchronize(dev)
     e2e_ms = max_over_ranks([s0.elapsed_time(s1) / args.e2e_steps], dev)[0]
 
@@ -510,7 +557,10 @@ def main():
     t_hbm_fwd = cnt.fwd_hbm_bytes / (hbm_peak * 1e9) * 1e6
     t_l2_fwd = cnt.fwd_l2_gather_bytes / (l2_gather_gbs * 1e9) * 1e6
     t_hbm_bwd = cnt.bwd_hbm_bytes / (hbm_peak * 1e9) * 1e6
-    t_l2_bwd = cnt.bwd_l2_bytes / (l2_gather_gbs * 1e9) * 1e6
+    red_bytes = cnt.bwd_l2_bytes - cnt.fwd_l2_gather_bytes
+    t_gather_bwd = cnt.fwd_l2_gather_bytes / (l2_gather_gbs * 1e9) * 1e6
+    t_red_bwd = red_bytes / (l2_red_gbs * 1e9) * 1e6
+    t_roof_bwd = max(t_hbm_bwd, t_gather_bwd, t_red_bwd)
     line = {
         "metric": METRIC, "value": us_per_frame, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
@@ -518,6 +568,7 @@ def main():
         "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": B, "parallelism": f"replicas x{world}",
                    "backward": "deterministic" if det else "atomic",
                    "grad_feat_clear": None if det else {
+                       "forward": "inside the forward kernel (msda_forward_train)",
                        "side": "torch fill on a side stream during the forward",
                        "inline": "memset inside msda_backward"}[args.clear],
                    "l2": "inputs larger than L2 (feat 355 MB, grad_feat 710 MB per frame); no flush"},
@@ -529,13 +580,16 @@ def main():
                      "algorithmic_bytes": dom_bytes},
         "gather_roofline": {
             "l2_gather_gbs_measured": l2_gather_gbs,
+            "l2_reduce_gbs_measured": l2_red_gbs,
             "fwd": {"t_hbm_us": t_hbm_fwd, "t_l2_us": t_l2_fwd, "t_roof_us": max(t_hbm_fwd, t_l2_fwd),
                     "t_us": fwd_ms * 1e3, "frac": max(t_hbm_fwd, t_l2_fwd) / (fwd_ms * 1e3)},
-            "bwd": {"t_hbm_us": t_hbm_bwd, "t_l2_us": t_l2_bwd, "t_roof_us": max(t_hbm_bwd, t_l2_bwd),
-                    "t_us": bwd_ms * 1e3, "frac": max(t_hbm_bwd, t_l2_bwd) / (bwd_ms * 1e3)}},
+            "bwd": {"t_hbm_us": t_hbm_bwd, "t_l2_gather_us": t_gather_bwd, "t_l2_reduce_us": t_red_bwd,
+                    "t_roof_us": t_roof_bwd, "t_us": bwd_ms * 1e3, "frac": t_roof_bwd / (bwd_ms * 1e3)}},
         "counts": cnt.as_dict(),
-        "e2e": {"value": e2e_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": ((2 if fwd_ws is not None else 1) + (1 if not det else 9)) * args.steps,
+        "e2e": {"value": e2e_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": args.e2e_steps,
+                "pipeline": "copy-in, compute and copy-out of consecutive steps overlap (3 streams, 2 buffer sets)"},
+        "gpu_launches": ((2 if fwd_ws is not None and not fwd_clear else 1) + (1 if not det else 9)) * args.steps,
         "tuning": {"forward": ft, "backward": bt},
         "clocks": clk.summary(),
         "gpu": torch.cuda.get_device_name(dev),
@@ -545,7 +599,7 @@ def main():
     if args.extras:
         line["extras"] = extras(pr, dev, ft)
     if args.configs:
-        line["other_workloads"] = other_configs(dev, l2_gather_gbs, hbm_peak)
+        line["other_workloads"] = other_configs(dev, l2_gather_gbs, l2_red_gbs, hbm_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, args.cpu_sample_anchors)
     if rank == 0:

@@ -132,6 +132,24 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype,
                          const msda_tuning* tuning, msda_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Forward of a training step: msda_forward (anchor-per-block kernel; the
+ * tuning fields as for msda_forward) that also sets grad_feat
+ * [B, sum_hw, C] (float32, 16-byte aligned; C a multiple of 4) to zero, for
+ * an atomic msda_backward called afterwards with MSDA_FLAG_GRAD_FEAT_ZEROED.
+ * The forward's blocks store the zeros in small pieces alongside their
+ * gathers, on HBM write bandwidth the forward leaves unused, instead of a
+ * separate memset before the backward.  With no anchors or no points the
+ * clearing is a memset on `stream`.
+ * ------------------------------------------------------------------------ */
+msda_status msda_forward_train(const void* feat, msda_dtype feat_dtype,
+                               const int32_t* spatial_shape, const int32_t* scale_start_index,
+                               const float* sampling_location,
+                               const void* weights, msda_dtype weights_dtype,
+                               void* out, msda_dtype out_dtype, float* grad_feat,
+                               int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,
+                               const msda_tuning* tuning, msda_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * msda_forward_oae - the operator followed by the occlusion-aware
  * visibility-weighted fusion over cameras (Sec. 3.2, Eq. 2), fused:
  *   out[b,a,:] = sum_k vis[b,a,k] * g_k / sum_k vis[b,a,k]
@@ -307,6 +325,14 @@ const char* msda_version(void);
  * ------------------------------------------------------------------------ */
 msda_status msda_probe_read(const void* buf, size_t bytes, int reps, int blocks, int rows,
                             uint32_t* sink, msda_stream_t stream);
+
+/* Measurement aid: FP32 reduction throughput.  In `blocks` blocks of 512
+ * threads, every warp adds 1.0 to `rows` pseudo-random 1 KB rows of `buf`
+ * (device FP32, 16-byte aligned, bytes a multiple of 1024; its contents are
+ * changed) per rep with 16-byte vector reductions, the scatter pattern of the
+ * atomic backward.  A buffer smaller than L2 measures the L2's reduction
+ * throughput, which bounds that backward. */
+msda_status msda_probe_reduce(float* buf, size_t bytes, int reps, int blocks, int rows, msda_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -202,6 +202,29 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype, const int32_t*
     return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream, nullptr, half_acc);
 }
 
+msda_status msda_forward_train(const void* feat, msda_dtype feat_dtype, const int32_t* spatial_shape,
+                               const int32_t* scale_start_index, const float* sampling_location,
+                               const void* weights, msda_dtype weights_dtype, void* out, msda_dtype out_dtype,
+                               float* grad_feat, int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P,
+                               int G, const msda_tuning* tuning, msda_stream_t stream) {
+    t_err[0] = 0;
+    Problem p;
+    msda_status st = validate("msda_forward_train", feat, feat_dtype, spatial_shape, scale_start_index,
+                              sampling_location, weights, weights_dtype, B, sum_hw, C, Ncam, Nscale, A, P, G, &p);
+    if (st != MSDA_OK) return st;
+    if (dtype_size(out_dtype) == 0) return fail(MSDA_ERR_INVALID_ARG, "msda_forward_train: unknown out dtype");
+    if ((long long)B * A > 0 && !out) return fail(MSDA_ERR_INVALID_ARG, "msda_forward_train: out is NULL");
+    if ((long long)B * sum_hw > 0 && !grad_feat)
+        return fail(MSDA_ERR_INVALID_ARG, "msda_forward_train: grad_feat is NULL");
+    if (!aligned16(out) || !aligned16(grad_feat))
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_train: out and grad_feat must be 16-byte aligned");
+    if (C % 4 != 0) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_train: C must be a multiple of 4");
+    prefer_split(tuning, &p, 2);
+    const bool half_acc = tuning && tuning->variant == 3;
+    return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream, nullptr, half_acc,
+                          grad_feat);
+}
+
 msda_status msda_forward_oae(const void* feat, msda_dtype feat_dtype, const int32_t* spatial_shape,
                              const int32_t* scale_start_index, const float* sampling_location,
                              const void* weights, msda_dtype weights_dtype, const float* visibility, void* out,
@@ -368,6 +391,14 @@ msda_status msda_probe_read(const void* buf, size_t bytes, int reps, int blocks,
         return fail(MSDA_ERR_INVALID_ARG, "msda_probe_read: bad arguments");
     if (!aligned16(buf) || !aligned16(sink)) return fail(MSDA_ERR_UNSUPPORTED, "msda_probe_read: alignment");
     return launch_probe(buf, bytes, reps, blocks, rows, sink, (cudaStream_t)stream);
+}
+
+msda_status msda_probe_reduce(float* buf, size_t bytes, int reps, int blocks, int rows, msda_stream_t stream) {
+    t_err[0] = 0;
+    if (!buf || reps < 1 || blocks < 1 || rows < 1 || bytes < 1024 || bytes % 1024)
+        return fail(MSDA_ERR_INVALID_ARG, "msda_probe_reduce: bad arguments");
+    if (!aligned16(buf)) return fail(MSDA_ERR_UNSUPPORTED, "msda_probe_reduce: alignment");
+    return launch_probe_reduce(buf, bytes, reps, blocks, rows, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -41,6 +41,8 @@ struct FwdArgs {
     int B, sum_hw, C, Ncam, Nscale, A, P, G, Cg;
     int rt;
     int* status;
+    uint4* zero;                   // msda_forward_train: grad_feat to clear (16-byte units), or NULL
+    unsigned long long zero_n16;
 };
 
 // Shared-memory carve-up of a forward block.
@@ -65,15 +67,30 @@ struct FwdSmem {
 // svn (optional): per-camera factor applied to every weight of the camera
 // (the normalised visibility of the fused occlusion-aware form); a camera
 // with factor 0 is skipped.
+// Clearing a slice of another buffer alongside (training forward): the team
+// handling item i also zeroes piece i of the block's slice [zlo, zhi) of
+// `zero` (16-byte units, zchunk per item, lanes tl of rt), so the stores
+// are spread evenly over the block's life.
+struct ZeroSlice {
+    uint4* ptr;
+    unsigned long long lo, hi, chunk;
+};
+
 template <typename FT, typename WT, int NV>
 __device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, const WT* __restrict__ wb,
                                                   const MapInfo* __restrict__ smap, const float4* __restrict__ sbox,
                                                   const float2* __restrict__ sloc, int C, int Ncam,
                                                   int Nscale, int P, int G, int team, int nteams,
-                                                  float2* acc, const float* __restrict__ svn = nullptr) {
+                                                  float2* acc, const float* __restrict__ svn = nullptr,
+                                                  const ZeroSlice* zs = nullptr, int tl = 0, int rt = 1) {
     constexpr int VEC = Elem<FT>::VEC;
     const int nitems = Ncam * P;
     for (int item = team; item < nitems; item += nteams) {
+        if (zs) {
+            const unsigned long long z0 = zs->lo + (unsigned long long)item * zs->chunk;
+            const unsigned long long z1 = min(z0 + zs->chunk, zs->hi);
+            for (unsigned long long j = z0 + tl; j < z1; j += rt) __stcs(zs->ptr + j, make_uint4(0u, 0u, 0u, 0u));
+        }
         const int k = item / P;
         const int pp = item - k * P;
         const float2 uv = sloc[pp * Ncam + k];
@@ -154,7 +171,7 @@ __device__ __forceinline__ void reduce_and_store(const float* spart, int nteams,
 // shapes, every anchor's block is resident at once: then all blocks walk the
 // cameras in the same order together and each camera's maps are read from
 // HBM about once.
-template <typename FT, typename WT, int NV>
+template <typename FT, typename WT, int NV, bool CLEAR>
 __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anchor_kernel(const FwdArgs p) {
     constexpr int CPL = Elem<FT>::VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -199,8 +216,25 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
     float2 acc[CPL / 2];
 #pragma unroll
     for (int j = 0; j < CPL / 2; ++j) acc[j] = make_float2(0.0f, 0.0f);
-    accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc,
-                                  p.vis ? svn : nullptr);
+    if constexpr (CLEAR) {
+        // training forward: this block's slice of grad_feat, one piece per item (the host guarantees items);
+        // the slice bounds live in shared memory, not in registers held across the item loop
+        __shared__ ZeroSlice s_zs;
+        if (threadIdx.x == 0) {
+            const unsigned long long per = (p.zero_n16 + gridDim.x - 1) / gridDim.x;
+            s_zs.ptr = p.zero;
+            s_zs.lo = min((unsigned long long)blockIdx.x * per, p.zero_n16);
+            s_zs.hi = min(s_zs.lo + per, p.zero_n16);
+            const unsigned long long nitems = (unsigned long long)p.Ncam * p.P;
+            s_zs.chunk = (s_zs.hi - s_zs.lo + nitems - 1) / nitems;
+        }
+        __syncthreads();
+        accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc,
+                                      p.vis ? svn : nullptr, &s_zs, lane & (p.rt - 1), p.rt);
+    } else {
+        accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc,
+                                      p.vis ? svn : nullptr);
+    }
 
     float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
@@ -410,12 +444,12 @@ __global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
 using FwdKernel = void (*)(const FwdArgs);
 using BatchedKernel = void (*)(const BatchedArgs);
 
-template <typename FT, typename WT>
+template <typename FT, typename WT, bool CLEAR>
 static FwdKernel fwd_pick_nv(int nv) {
     switch (nv) {
-        case 1: return fwd_anchor_kernel<FT, WT, 1>;
-        case 2: return fwd_anchor_kernel<FT, WT, 2>;
-        case 4: return fwd_anchor_kernel<FT, WT, 4>;
+        case 1: return fwd_anchor_kernel<FT, WT, 1, CLEAR>;
+        case 2: return fwd_anchor_kernel<FT, WT, 2, CLEAR>;
+        case 4: return fwd_anchor_kernel<FT, WT, 4, CLEAR>;
     }
     return nullptr;
 }
@@ -431,12 +465,13 @@ static BatchedKernel batched_pick_nv(int nv) {
 }
 
 // Supported (feature, weight) dtype pairs: weights in FP32 or in the feature dtype.
+template <bool CLEAR>
 static FwdKernel fwd_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
-    if (ft == MSDA_F32 && wt == MSDA_F32) return fwd_pick_nv<float, float>(nv);
-    if (ft == MSDA_BF16 && wt == MSDA_BF16) return fwd_pick_nv<__nv_bfloat16, __nv_bfloat16>(nv);
-    if (ft == MSDA_BF16 && wt == MSDA_F32) return fwd_pick_nv<__nv_bfloat16, float>(nv);
-    if (ft == MSDA_F16 && wt == MSDA_F16) return fwd_pick_nv<__half, __half>(nv);
-    if (ft == MSDA_F16 && wt == MSDA_F32) return fwd_pick_nv<__half, float>(nv);
+    if (ft == MSDA_F32 && wt == MSDA_F32) return fwd_pick_nv<float, float, CLEAR>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_BF16) return fwd_pick_nv<__nv_bfloat16, __nv_bfloat16, CLEAR>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_F32) return fwd_pick_nv<__nv_bfloat16, float, CLEAR>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F16) return fwd_pick_nv<__half, __half, CLEAR>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F32) return fwd_pick_nv<__half, float, CLEAR>(nv);
     return nullptr;
 }
 
@@ -450,18 +485,24 @@ static BatchedKernel batched_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
 }
 
 msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int warps,
-                           cudaStream_t stream, const float* vis, bool half_acc) {
+                           cudaStream_t stream, const float* vis, bool half_acc, float* clear) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);
     if (st != MSDA_OK) return st;
-    FwdKernel k = fwd_kernel_for(p.feat_t, p.w_t, p.nv);
-    if (half_acc) {
-        if (p.feat_t != MSDA_F16 || p.w_t != MSDA_F16 || vis)
-            return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: half2 accumulation needs FP16 features and weights");
-        k = p.nv == 1 ? fwd_anchor_h2_kernel<1> : p.nv == 2 ? fwd_anchor_h2_kernel<2> : fwd_anchor_h2_kernel<4>;
-    }
-    if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: unsupported feature/weight dtype pair");
+    if (half_acc && (p.feat_t != MSDA_F16 || p.w_t != MSDA_F16 || vis))
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: half2 accumulation needs FP16 features and weights");
     const long long nblocks = (long long)p.B * p.A;
+    const size_t clear_bytes = sizeof(float) * (size_t)p.B * p.sum_hw * p.C;
+    if (clear && (clear_bytes == 0 || nblocks == 0 || (long long)p.Ncam * p.P == 0 || half_acc)) {
+        // no items to carry the clearing (or the half2 kernel, which does not clear): a plain memset
+        if (clear_bytes && cudaMemsetAsync(clear, 0, clear_bytes, stream) != cudaSuccess)
+            return check_launch("msda_forward_train");
+        clear = nullptr;
+    }
+    // the clearing kernel is chosen only when `clear` is still set, so its slice pointer is never NULL
+    FwdKernel k = clear ? fwd_kernel_for<true>(p.feat_t, p.w_t, p.nv) : fwd_kernel_for<false>(p.feat_t, p.w_t, p.nv);
+    if (half_acc) k = p.nv == 1 ? fwd_anchor_h2_kernel<1> : p.nv == 2 ? fwd_anchor_h2_kernel<2> : fwd_anchor_h2_kernel<4>;
+    if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: unsupported feature/weight dtype pair");
     if (nblocks == 0) return MSDA_OK;
     if (nblocks > 0x7fffffffLL) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: B*A too large");
     const int nteams = warps * (32 / p.rt);
@@ -473,6 +514,8 @@ msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int wa
     a.out = out; a.out_t = out_t;
     a.B = p.B; a.sum_hw = p.sum_hw; a.C = p.C; a.Ncam = p.Ncam; a.Nscale = p.Nscale;
     a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.status = dev.status;
+    a.zero = reinterpret_cast<uint4*>(clear);
+    a.zero_n16 = clear ? clear_bytes / 16 : 0;
     k<<<(unsigned)nblocks, warps * 32, lay.total, stream>>>(a);
     return check_launch("msda_forward");
 }

@@ -54,7 +54,8 @@ int dtype_size(msda_dtype t);
 // 0 = no feature gradient, 1 = clear grad_feat then scatter, 2 = scatter
 // into a grad_feat the caller already cleared.
 msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int warps,
-                           cudaStream_t stream, const float* vis = nullptr, bool half_acc = false);
+                           cudaStream_t stream, const float* vis = nullptr, bool half_acc = false,
+                           float* clear = nullptr);
 msda_status launch_backward_atomic(const Problem& p, const float* grad_out, float* grad_feat,
                                    float* grad_loc, float* grad_w, void* ws, size_t ws_bytes, int warps,
                                    bool zeroed, cudaStream_t stream);
@@ -85,6 +86,7 @@ msda_status launch_backward_cg(const Problem& p, const float* grad_out, float* g
                                float* grad_w, void* ws, size_t ws_bytes, cudaStream_t stream);
 msda_status launch_keypoints(const float* anchors, const float* offsets, const float* dt, const float* proj,
                              const float* img_wh, float* loc, int B, int A, int P, int Ncam, cudaStream_t stream);
+msda_status launch_probe_reduce(float* buf, size_t bytes, int reps, int blocks, int rows, cudaStream_t stream);
 msda_status launch_probe(const void* buf, size_t bytes, int reps, int blocks, int rows,
                          uint32_t* sink, cudaStream_t stream);
 

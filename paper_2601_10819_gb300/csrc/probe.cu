@@ -1,4 +1,4 @@
-// Read-bandwidth probes (a measurement aid; no counterpart in the paper).
+// Bandwidth probes (a measurement aid; no counterpart in the paper).
 //
 // The operator is a gather: it reads each feature row about ten times, so
 // its speed is set by how fast the SMs can pull 16-byte chunks of random
@@ -63,6 +63,33 @@ __global__ void __launch_bounds__(512) probe_gather_kernel(const uint4* __restri
         }
     }
     if (acc == 0x9e3779b9u) sink[blockIdx.x] = acc;
+}
+
+// Reduction probe: every warp adds 1.0 to `rows` pseudo-random 1 KB rows of FP32 per rep with 16-byte vector
+// reductions (red.global.add.v4.f32, two per lane and row), the scatter pattern of the atomic backward.  With
+// a buffer that fits in L2 it measures the L2's FP32 reduction throughput.
+__global__ void __launch_bounds__(512) probe_reduce_kernel(float* __restrict__ buf, uint32_t nrows, int reps,
+                                                           int rows) {
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < reps; ++r) {
+        for (int j = 0; j < rows; ++j) {
+            const uint32_t row = mix32(gw * 0x9e3779b9u + (uint32_t)(r * rows + j)) % nrows;
+            float* base = buf + (size_t)row * 256 + 4 * lane;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                             :: "l"(__cvta_generic_to_global(base + 128 * h)), "f"(1.0f), "f"(1.0f), "f"(1.0f),
+                                "f"(1.0f));
+        }
+    }
+}
+
+msda_status launch_probe_reduce(float* buf, size_t bytes, int reps, int blocks, int rows, cudaStream_t stream) {
+    const size_t nrows = bytes / 1024;
+    if (nrows == 0 || nrows > 0xffffffffull) return fail(MSDA_ERR_INVALID_ARG, "msda_probe_reduce: rows");
+    probe_reduce_kernel<<<blocks, 512, 0, stream>>>(buf, (uint32_t)nrows, reps, rows);
+    return check_launch("msda_probe_reduce");
 }
 
 msda_status launch_probe(const void* buf, size_t bytes, int reps, int blocks, int rows, uint32_t* sink,

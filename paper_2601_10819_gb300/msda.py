@@ -76,6 +76,8 @@ def load(path: Optional[str] = None):
         lib.msda_forward.restype = i
         lib.msda_forward_oae.argtypes = [vp, i, vp, vp, vp, vp, i, vp, vp, i] + [i] * 8 + [tp, vp]
         lib.msda_forward_oae.restype = i
+        lib.msda_forward_train.argtypes = [vp, i, vp, vp, vp, vp, i, vp, i, vp] + [i] * 8 + [tp, vp]
+        lib.msda_forward_train.restype = i
         lib.msda_keypoints.argtypes = [vp] * 6 + [i] * 4 + [vp]
         lib.msda_keypoints.restype = i
         lib.msda_backward_workspace_size.argtypes = [i] * 9
@@ -94,6 +96,8 @@ def load(path: Optional[str] = None):
         lib.msda_version.restype = ctypes.c_char_p
         lib.msda_probe_read.argtypes = [vp, sz, i, i, i, vp, vp]
         lib.msda_probe_read.restype = i
+        lib.msda_probe_reduce.argtypes = [vp, sz, i, i, i, vp]
+        lib.msda_probe_reduce.restype = i
         if path is None:
             _lib = lib
         return lib
@@ -183,6 +187,28 @@ def forward(feat, spatial_shape, scale_start_index, sampling_location, weights, 
                           B, sum_hw, C, Ncam, Nscale, A, P, G, _ptr(workspace), ws_bytes, _tuning(warps, None, variant, vec),
                           ctypes.c_void_p(_stream(feat.device)))
     _check("msda_forward", rc)
+    return out
+
+
+def forward_train(feat, spatial_shape, scale_start_index, sampling_location, weights, grad_feat, *,
+                  out: Optional[torch.Tensor] = None, out_dtype: torch.dtype = torch.float32,
+                  warps: Optional[int] = None, variant: int = 0, vec: int = 0) -> torch.Tensor:
+    """msda_forward_train: the forward, also clearing grad_feat (float32 [B, sum_hw, C]) for a following
+    backward(..., grads=(grad_feat, ...), grad_feat_zeroed=True)."""
+    lib = load()
+    B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
+    if grad_feat.dtype != torch.float32 or not grad_feat.is_cuda or not grad_feat.is_contiguous() or \
+            tuple(grad_feat.shape) != (B, sum_hw, C):
+        raise ValueError("grad_feat must be a contiguous float32 CUDA tensor [B, sum_hw, C]")
+    if out is None:
+        out = torch.empty(B, A, C, dtype=out_dtype, device=feat.device)
+    elif out.shape != (B, A, C) or not out.is_contiguous() or out.dtype not in _DT:
+        raise ValueError("out must be a contiguous [B, A, C] tensor")
+    rc = lib.msda_forward_train(_ptr(feat), _DT[feat.dtype], _ptr(spatial_shape), _ptr(scale_start_index),
+                                _ptr(sampling_location), _ptr(weights), _DT[weights.dtype], _ptr(out), _DT[out.dtype],
+                                _ptr(grad_feat), B, sum_hw, C, Ncam, Nscale, A, P, G,
+                                _tuning(warps, None, variant, vec), ctypes.c_void_p(_stream(feat.device)))
+    _check("msda_forward_train", rc)
     return out
 
 
@@ -287,6 +313,15 @@ def probe_read(buf: torch.Tensor, reps: int, blocks: int, rows: int = 0, sink: O
                              ctypes.c_void_p(_stream(buf.device)))
     _check("msda_probe_read", rc)
     return sink
+
+
+def probe_reduce(buf: torch.Tensor, reps: int, blocks: int, rows: int):
+    """msda_probe_reduce on a float32 CUDA buffer (its contents change)."""
+    lib = load()
+    if buf.dtype != torch.float32 or not buf.is_contiguous():
+        raise ValueError("probe_reduce needs a contiguous float32 buffer")
+    rc = lib.msda_probe_reduce(_ptr(buf), buf.numel() * 4, reps, blocks, rows, ctypes.c_void_p(_stream(buf.device)))
+    _check("msda_probe_reduce", rc)
 
 
 # ---------------------------------------------------------------------------

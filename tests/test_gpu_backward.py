@@ -299,3 +299,38 @@ def test_side_stream_clear_then_zeroed_backward():
     assert relerr(g[0].double().numpy(), ref[0].double().numpy()) <= 1e-6
     assert torch.equal(g[1], ref[1]) and torch.equal(g[2], ref[2])
     assert msda.device_status() == 0
+
+
+@pytest.mark.parametrize("case", ["tiny", "sparse4d-200", "no-anchors", "no-points", "half2"])
+def test_forward_train_clears_grad_feat_and_matches_forward(case):
+    """msda_forward_train: the same output as msda_forward (bitwise: same kernel and mapping) and a grad_feat of
+    zeros (it starts as NaN), so that the zeroed-flag backward equals a backward that clears by itself."""
+    if case == "tiny":
+        pr = inputs.make_workload(0)
+    elif case == "sparse4d-200":
+        pr = inputs.make_workload(1, feat_dtype="bf16", w_dtype="bf16").anchors(range(200))
+    elif case == "half2":
+        pr = inputs.make_workload(1, feat_dtype="f16", w_dtype="f16").anchors(range(50))
+    else:
+        gen = torch.Generator().manual_seed(5)
+        A, P = (0, 3) if case == "no-anchors" else (7, 0)
+        pr = inputs.make_problem(gen, B=2, cam_maps=[[(6, 5), (3, 2)]] * 2, C=32, G=4, A=A, P=P)
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    B, sum_hw, C = d.feat.shape
+    variant = 3 if case == "half2" else 0
+    gf = torch.full((B, sum_hw, C), float("nan"), device="cuda")
+    for warps in (2, 8):
+        gf.fill_(float("nan"))
+        got = msda.forward_train(*T, gf, warps=warps, variant=variant)
+        ref = msda.forward(*T, warps=warps, variant=variant)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), case
+        assert torch.all(gf == 0), case
+    if d.grad_out is not None and case in ("tiny", "sparse4d-200"):
+        refg = [t.cpu() for t in msda.backward(*T, d.grad_out)]
+        gl, gw = torch.empty(d.sampling_location.shape, device="cuda"), torch.empty(d.weights.shape, device="cuda")
+        g = [t.cpu() for t in msda.backward(*T, d.grad_out, grads=(gf, gl, gw), grad_feat_zeroed=True)]
+        assert relerr(g[0].double().numpy(), refg[0].double().numpy()) <= 1e-6
+        assert torch.equal(g[1], refg[1]) and torch.equal(g[2], refg[2])
+    assert msda.device_status() == 0
