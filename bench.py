@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--copy-streams", type=int, default=1, help="streams per copy direction in the end-to-end run")
     ap.add_argument("--cpu-sample-anchors", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deterministic", action="store_true", help="time the deterministic backward instead")
@@ -506,28 +507,37 @@ def main():
         d_out = [torch.empty_like(x) for x in (out, gf, gl, gw)]
         slots.append((d_in, d_out, [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in d_out]))
     d2h = sum(x.numel() * x.element_size() for x in slots[0][2])
-    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    ev_in, ev_comp, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+    nsplit = max(1, args.copy_streams)
+    s_in = [torch.cuda.Stream(dev) for _ in range(nsplit)]
+    s_out = [torch.cuda.Stream(dev) for _ in range(nsplit)]
+    ev_in, ev_comp, ev_out = ([[torch.cuda.Event() for _ in range(nsplit)] for _ in range(2)] for _ in range(3))
+
+    def split_copy(dsts, srcs, streams, wait, done):
+        # every tensor cut into len(streams) contiguous pieces, piece q on stream q
+        for q, st in enumerate(streams):
+            st.wait_event(wait)
+            with torch.cuda.stream(st):
+                for dd, ss in zip(dsts, srcs):
+                    n = dd.numel()
+                    lo, hi = n * q // len(streams), n * (q + 1) // len(streams)
+                    if hi > lo:
+                        dd.view(-1)[lo:hi].copy_(ss.view(-1)[lo:hi], non_blocking=True)
+            done[q].record(st)
 
     def e2e_step(i):
         j = i % 2
         d_in, d_out, h_out = slots[j]
-        s_in.wait_event(ev_comp[j])  # the compute that last read this slot's inputs is done
-        with torch.cuda.stream(s_in):
-            for h, dd in zip(h_in, d_in):
-                dd.copy_(h, non_blocking=True)
-        ev_in[j].record(s_in)
-        main.wait_event(ev_in[j])
-        main.wait_event(ev_out[j])   # this slot's outputs have been copied out
+        # copy-in waits until the compute that last read this slot's inputs is done
+        split_copy(d_in, h_in, s_in, ev_comp[j][0], ev_in[j])
+        for e in ev_in[j]:
+            main.wait_event(e)
+        for e in ev_out[j]:
+            main.wait_event(e)  # this slot's outputs have been copied out
         tens = (d_in[0], d.spatial_shape, d.scale_start_index, d_in[1], d_in[2])
         fwd(tens, d_out)
         bwd(tens, d_in[3], d_out)
-        ev_comp[j].record(main)
-        s_out.wait_event(ev_comp[j])
-        with torch.cuda.stream(s_out):
-            for h, dd in zip(h_out, d_out):
-                h.copy_(dd, non_blocking=True)
-        ev_out[j].record(s_out)
+        ev_comp[j][0].record(main)
+        split_copy(h_out, d_out, s_out, ev_comp[j][0], ev_out[j])
 
     for i in range(2):
         e2e_step(i)
@@ -538,7 +548,8 @@ def main():
     s0.record(main)
     for i in range(args.e2e_steps):
         e2e_step(i)
-    main.wait_stream(s_out)
+    for st in s_out:
+        main.wait_stream(st)
     s1.record(main)
     torch.cuda.synchronize(dev)
     e2e_ms = max_over_ranks([s0.elapsed_time(s1) / args.e2e_steps], dev)[0]
@@ -588,7 +599,8 @@ def main():
         "counts": cnt.as_dict(),
         "e2e": {"value": e2e_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps,
-                "pipeline": "copy-in, compute and copy-out of consecutive steps overlap (3 streams, 2 buffer sets)"},
+                "pipeline": f"copy-in, compute and copy-out of consecutive steps overlap (2 buffer sets; each "
+                            f"direction's copies cut over {nsplit} streams)"},
         "gpu_launches": ((2 if fwd_ws is not None and not fwd_clear else 1) + (1 if not det else 9)) * args.steps,
         "tuning": {"forward": ft, "backward": bt},
         "clocks": clk.summary(),

@@ -89,8 +89,8 @@ typedef struct {
                               2 = staged camera-group form                   */
     int vectors_per_lane;  /* 16-byte feature vectors per lane and corner row
                               (1, 2 or 4): more work per lane, fewer lanes
-                              per point; 0 = built-in default (forward 2,
-                              backward 1), else the smallest valid split     */
+                              per point; 0 = built-in default (2 when that
+                              split is valid), else the smallest valid split */
     int flags;             /* MSDA_FLAG_* bits                                */
     int reserved[3];
 } msda_tuning;

@@ -277,7 +277,7 @@ msda_status msda_backward(const void* feat, msda_dtype feat_dtype, const int32_t
     if (!aligned16(grad_out) || !aligned16(grad_feat) || !aligned16(grad_loc) || !aligned16(grad_weights))
         return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: gradient pointers must be 16-byte aligned");
     if (p.C % 4 != 0) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: C must be a multiple of 4");
-    prefer_split(tuning, &p, 0);
+    prefer_split(tuning, &p, 2);
     const int warps = pick_warps(tuning, 4);
     if (deterministic) {
         if (workspace && !aligned16(workspace))

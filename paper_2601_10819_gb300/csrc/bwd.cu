@@ -57,7 +57,9 @@ __device__ __forceinline__ float team_sum(float v, unsigned mask, int width) {
     return v;
 }
 
-template <typename FT, typename WT, int NV>
+// SCATTER = false builds the form without the feature-gradient reductions (the deterministic modes take
+// dloc and dw from it), which needs fewer registers.
+template <typename FT, typename WT, int NV, bool SCATTER>
 __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
     constexpr int VEC = Elem<FT>::VEC;
     constexpr int CPL = VEC * NV;
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
                 dwp = o00 * d00 + o01 * d01 + o10 * d10 + o11 * d11;
                 du = fmaf((float)m.W * wvs, ay * (d01 - d00) + c.fy * (d11 - d10), du);
                 dv = fmaf((float)m.H * wvs, ax * (d10 - d00) + c.fx * (d11 - d01), dv);
-                if (p.scatter) {
+                if (SCATTER && p.scatter) {
                     // feature gradient w * omega * go, in the interleaved layout: each warp-wide
                     // 16-byte vector atomic covers 4*rt contiguous channels (whole sectors);
                     // an interleaved chunk belongs to its own group, with its own weight
@@ -220,22 +222,23 @@ __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
 
 using BwdKernel = void (*)(const BwdArgs);
 
-template <typename FT, typename WT>
+template <typename FT, typename WT, bool SCATTER>
 static BwdKernel bwd_pick_nv(int nv) {
     switch (nv) {
-        case 1: return bwd_atomic_kernel<FT, WT, 1>;
-        case 2: return bwd_atomic_kernel<FT, WT, 2>;
-        case 4: return bwd_atomic_kernel<FT, WT, 4>;
+        case 1: return bwd_atomic_kernel<FT, WT, 1, SCATTER>;
+        case 2: return bwd_atomic_kernel<FT, WT, 2, SCATTER>;
+        case 4: return bwd_atomic_kernel<FT, WT, 4, SCATTER>;
     }
     return nullptr;
 }
 
+template <bool SCATTER>
 static BwdKernel bwd_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
-    if (ft == MSDA_F32 && wt == MSDA_F32) return bwd_pick_nv<float, float>(nv);
-    if (ft == MSDA_BF16 && wt == MSDA_BF16) return bwd_pick_nv<__nv_bfloat16, __nv_bfloat16>(nv);
-    if (ft == MSDA_BF16 && wt == MSDA_F32) return bwd_pick_nv<__nv_bfloat16, float>(nv);
-    if (ft == MSDA_F16 && wt == MSDA_F16) return bwd_pick_nv<__half, __half>(nv);
-    if (ft == MSDA_F16 && wt == MSDA_F32) return bwd_pick_nv<__half, float>(nv);
+    if (ft == MSDA_F32 && wt == MSDA_F32) return bwd_pick_nv<float, float, SCATTER>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_BF16) return bwd_pick_nv<__nv_bfloat16, __nv_bfloat16, SCATTER>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_F32) return bwd_pick_nv<__nv_bfloat16, float, SCATTER>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F16) return bwd_pick_nv<__half, __half, SCATTER>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F32) return bwd_pick_nv<__half, float, SCATTER>(nv);
     return nullptr;
 }
 
@@ -257,7 +260,7 @@ msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float
     DeviceInfo dev;
     msda_status st = device_info(&dev);
     if (st != MSDA_OK) return st;
-    BwdKernel k = bwd_kernel_for(p.feat_t, p.w_t, p.nv);
+    BwdKernel k = scatter ? bwd_kernel_for<true>(p.feat_t, p.w_t, p.nv) : bwd_kernel_for<false>(p.feat_t, p.w_t, p.nv);
     if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: unsupported feature/weight dtype pair");
     const size_t feat_bytes = sizeof(float) * (size_t)p.B * p.sum_hw * p.C;
     if (scatter == 1 && feat_bytes && cudaMemsetAsync(grad_feat, 0, feat_bytes, stream) != cudaSuccess)

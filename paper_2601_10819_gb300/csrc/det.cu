@@ -4,15 +4,19 @@
 // point adds w_g * omega * go[c] to one feature row.  Scattering with
 // atomics makes the FP32 summation order depend on timing.  This mode
 // instead gathers: it builds, for every corner of every point-scale, the
-// key (feature row) and the value (the corner's slot id 4*pt + q), sorts
-// the pairs by key with a stable LSD radix sort, so that equal rows keep the
-// slot order, and then lets one team per feature row sum its contributions
-// in that order and write the row once (rows nobody touches get zeros, so
-// no memset is needed).  The result is bitwise reproducible for any launch.
+// key (feature row) and the value (the corner's slot id), sorts the pairs by
+// key with a stable LSD radix sort, so that equal rows keep the slot order,
+// turns the sorted slots into flat (omega, point-scale, anchor row) arrays,
+// and then lets one team per feature row sum its contributions in that
+// order and write the row once (rows nobody touches get zeros, so no memset
+// is needed).  The result is bitwise reproducible for any launch.
 //
-// Point-scale index pt = ((((b*A + a)*P + p)*Ncam + k)*Nscale + s).  The
-// reduce kernel recomputes the corner weight omega from the location with
-// the same arithmetic as every other kernel, so keys and weights agree.
+// Point index t = (((b*A + a)*P + p)*Ncam + k); a corner's slot id packs
+// (t, s, q) as (t << (sbits + 2)) | (s << 2) | q, with sbits the bits of
+// Nscale - 1, so slot order is (t, s, q) order and the reduce decodes a slot
+// with shifts and two divisions by constants (multiply-high).  The reduce
+// kernel recomputes the corner weight omega from the location with the same
+// arithmetic as every other kernel, so keys and weights agree.
 #include "common.cuh"
 #include "internal.h"
 
@@ -66,10 +70,35 @@ struct KeyArgs {
     uint32_t* keys;
     uint32_t* vals;
     long long npts;
-    int sum_hw, A, P, Ncam, Nscale;
+    int sum_hw, A, P, Ncam, Nscale, sbits;
     uint32_t sentinel;
     int* status;
 };
+
+// Division by a fixed d >= 1 for numerators below 2^31 (the round-up method
+// of Granlund and Montgomery): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l; the sum
+// stays below 2^32 because umulhi(n, m) <= n.
+struct FastDiv {
+    uint32_t d, m, l;
+};
+
+static FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    f.l = 0;
+    while ((1ull << f.l) < d) ++f.l;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << f.l) - d)) / d) + 1ull);
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.l; }
+
+static int scale_bits(int Nscale) {
+    int b = 0;
+    while ((1 << b) < Nscale) ++b;
+    return b;
+}
 
 __global__ void __launch_bounds__(256) det_keys_kernel(const KeyArgs a) {
     for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < a.npts;
@@ -89,7 +118,7 @@ __global__ void __launch_bounds__(256) det_keys_kernel(const KeyArgs a) {
             const bool ok = in && i >= 0 && i < m.H && j >= 0 && j < m.W;
             key[q] = ok ? (uint32_t)(b * a.sum_hw + m.start + i * m.W + j) : a.sentinel;
         }
-        const uint32_t slot = (uint32_t)(pt * 4);
+        const uint32_t slot = (((uint32_t)t << a.sbits) | (uint32_t)s) << 2;
         reinterpret_cast<uint4*>(a.keys)[pt] = make_uint4(key[0], key[1], key[2], key[3]);
         reinterpret_cast<uint4*>(a.vals)[pt] = make_uint4(slot, slot + 1, slot + 2, slot + 3);
     }
@@ -226,20 +255,52 @@ struct RedArgs {
     const float* go;
     const uint32_t* vals;
     const uint32_t* rowptr;
+    const float* e_om;       // per sorted contribution: bilinear weight omega of its corner
+    const uint32_t* e_pt;    //   point-scale index (t * Nscale + s)
+    const uint32_t* e_ba;    //   anchor row b * A + a of grad_out
     float* gfeat;
     long long nrows;
-    int sum_hw, C, Ncam, Nscale, A, P, G, Cg, rt;
+    int sum_hw, C, Ncam, Nscale, A, P, G, Cg, rt, sbits;
+    FastDiv ncam, pncam;  // divisions by Ncam and P*Ncam
     int* status;
 };
 
-template <typename WT, int CPL>
-__global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
+// Per sorted contribution e (in key order, valid keys only): decode the slot, recompute the corner weight
+// omega from the location, and store (omega, point-scale, anchor row) in three flat arrays, so that the row
+// reduce reads them contiguously instead of chasing slot -> location -> cell for every contribution.
+__global__ void __launch_bounds__(256) det_prep_kernel(RedArgs a, size_t n, float* om_out, uint32_t* pt_out,
+                                                       uint32_t* ba_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem);
     const int nmaps = a.Ncam * a.Nscale;
     for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
         smap[i] = load_map(a.shape, a.start, i, a.sum_hw, nullptr);
     __syncthreads();
+    const size_t nvalid = a.rowptr[a.nrows];  // the sentinel keys sort after every row
+    const uint32_t smask = (1u << a.sbits) - 1u;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nvalid && e < n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t v = __ldg(a.vals + e);
+        const int q = (int)(v & 3u);
+        const int s = (int)((v >> 2) & smask);
+        const uint32_t t = v >> (a.sbits + 2);
+        const int k = (int)(t - fdiv(t, a.ncam) * (uint32_t)a.Ncam);
+        const MapInfo m = smap[k * a.Nscale + s];
+        const float2 uv = __ldg(reinterpret_cast<const float2*>(a.loc) + t);
+        Cell c;
+        locate(uv.x, uv.y, m.H, m.W, c);  // in range: the key was valid
+        const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
+        om_out[e] = (q == 0) ? ax * ay : (q == 1) ? c.fx * ay : (q == 2) ? ax * c.fy : c.fx * c.fy;
+        pt_out[e] = t * (uint32_t)a.Nscale + (uint32_t)s;
+        ba_out[e] = fdiv(t, a.pncam);
+    }
+}
+
+// One team of rt lanes per feature row sums its contributions in sorted (slot) order; U contributions are
+// loaded together, then added in order.
+template <typename WT, int CPL>
+__global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
+    constexpr int U = CPL >= 32 ? 1 : 32 / CPL;
     const int tpw = 32 / a.rt;
     const int nteams = (blockDim.x >> 5) * tpw;
     const int lane = threadIdx.x & 31;
@@ -253,30 +314,28 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
 #pragma unroll
     for (int j = 0; j < CPL; ++j) acc[j] = 0.0f;
     const uint32_t e0 = a.rowptr[row], e1 = a.rowptr[row + 1];
-    const long long per_anchor = (long long)a.P * a.Ncam;
-    for (uint32_t e = e0; e < e1; ++e) {
-        const uint32_t slot = __ldg(a.vals + e);
-        const long long pt = slot >> 2;
-        const int q = (int)(slot & 3u);
-        const int s = (int)(pt % a.Nscale);
-        const long long t = pt / a.Nscale;
-        const int k = (int)(t % a.Ncam);
-        const long long ba = t / per_anchor;
-        const MapInfo m = smap[k * a.Nscale + s];
-        const float2 uv = __ldg(reinterpret_cast<const float2*>(a.loc) + t);
-        Cell c;
-        locate(uv.x, uv.y, m.H, m.W, c);  // in range: the key was valid
-        const float ax = 1.0f - c.fx, ay = 1.0f - c.fy;
-        const float om = (q == 0) ? ax * ay : (q == 1) ? c.fx * ay : (q == 2) ? ax * c.fy : c.fx * c.fy;
-        const float coef = ldw(wp + pt * a.G + g) * om;
-        const float4* gsrc = reinterpret_cast<const float4*>(a.go + ba * a.C + c0);
+    for (uint32_t e = e0; e < e1; e += U) {
+        float coef[U];
+        float4 gv[U][CPL / 4];
 #pragma unroll
-        for (int j = 0; j < CPL / 4; ++j) {
-            const float4 v = __ldg(gsrc + j);
-            acc[4 * j + 0] = fmaf(coef, v.x, acc[4 * j + 0]);
-            acc[4 * j + 1] = fmaf(coef, v.y, acc[4 * j + 1]);
-            acc[4 * j + 2] = fmaf(coef, v.z, acc[4 * j + 2]);
-            acc[4 * j + 3] = fmaf(coef, v.w, acc[4 * j + 3]);
+        for (int u = 0; u < U; ++u) {
+            const uint32_t eu = (e + u < e1) ? e + u : e;  // the tail repeats a valid entry, not added below
+            coef[u] = ldw(wp + (long long)__ldg(a.e_pt + eu) * a.G + g) * __ldg(a.e_om + eu);
+            const float4* gsrc = reinterpret_cast<const float4*>(a.go + (long long)__ldg(a.e_ba + eu) * a.C + c0);
+#pragma unroll
+            for (int j = 0; j < CPL / 4; ++j) gv[u][j] = __ldg(gsrc + j);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (e + u < e1) {
+#pragma unroll
+                for (int j = 0; j < CPL / 4; ++j) {
+                    acc[4 * j + 0] = fmaf(coef[u], gv[u][j].x, acc[4 * j + 0]);
+                    acc[4 * j + 1] = fmaf(coef[u], gv[u][j].y, acc[4 * j + 1]);
+                    acc[4 * j + 2] = fmaf(coef[u], gv[u][j].z, acc[4 * j + 2]);
+                    acc[4 * j + 3] = fmaf(coef[u], gv[u][j].w, acc[4 * j + 3]);
+                }
+            }
         }
     }
     float4* dst = reinterpret_cast<float4*>(a.gfeat + row * a.C + c0);
@@ -305,12 +364,25 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     if (st != MSDA_OK) return st;
     const long long npts = (long long)p.B * p.A * p.P * p.Ncam * p.Nscale;
     const long long nrows = (long long)p.B * p.sum_hw;
-    if (npts * 4 >= (1ll << 32) || nrows >= (1ll << 32) - 1)
-        return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: deterministic mode limited to 2^32 corner slots and rows");
+    const int sbits = scale_bits(p.Nscale);
+    const long long npoints = (long long)p.B * p.A * p.P * p.Ncam;
+    if (npts * 4 >= (1ll << 32) || (npoints << (sbits + 2)) >= (1ll << 31) || nrows >= (1ll << 32) - 1)
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: deterministic mode limited to 2^31 corner slots and 2^32 rows");
     const DetLayout L = det_layout(npts, nrows);
     if (!ws || ws_bytes < L.total)
         return fail(MSDA_ERR_WORKSPACE, "msda_backward: deterministic mode needs %zu workspace bytes", L.total);
-    const int cpl = p.C / p.rt;
+    // The row reduce has its own lane split, independent of the gather kernel's: 8 channels per lane when C
+    // and the group width allow it (measured fastest: short rows of ~10 contributions favour many lanes),
+    // else the split of the gather kernel.
+    int red_rt = p.rt;
+    for (int cand : {8, 4, 16, 32}) {
+        const int r = p.C / cand;
+        if (p.C % cand == 0 && p.Cg % cand == 0 && r >= 1 && r <= 32 && (r & (r - 1)) == 0) {
+            red_rt = r;
+            break;
+        }
+    }
+    const int cpl = p.C / red_rt;
     RedKernel red = (p.w_t == MSDA_F32) ? red_pick<float>(cpl)
                   : (p.w_t == MSDA_BF16) ? red_pick<__nv_bfloat16>(cpl) : red_pick<__half>(cpl);
     if (!red) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: no reduce kernel for %d channels per lane", cpl);
@@ -331,7 +403,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
         KeyArgs ka;
         ka.shape = p.shape; ka.start = p.start; ka.loc = p.loc; ka.keys = kbuf[0]; ka.vals = vbuf[0];
         ka.npts = npts; ka.sum_hw = p.sum_hw; ka.A = p.A; ka.P = p.P; ka.Ncam = p.Ncam;
-        ka.Nscale = p.Nscale; ka.sentinel = (uint32_t)nrows; ka.status = dev.status;
+        ka.Nscale = p.Nscale; ka.sbits = sbits; ka.sentinel = (uint32_t)nrows; ka.status = dev.status;
         long long kb = (npts + 255) / 256;
         if (kb > (long long)dev.sm_count * 64) kb = (long long)dev.sm_count * 64;
         det_keys_kernel<<<(unsigned)kb, 256, 0, stream>>>(ka);
@@ -355,13 +427,26 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     RedArgs ra;
     ra.shape = p.shape; ra.start = p.start; ra.loc = p.loc; ra.w = p.w; ra.go = grad_out;
     ra.vals = vbuf[cur]; ra.rowptr = rowptr; ra.gfeat = grad_feat; ra.nrows = nrows;
+    // the sorted keys and the other sort buffers are free once the row offsets exist
+    ra.e_om = reinterpret_cast<const float*>(kbuf[cur ^ 1]);
+    ra.e_pt = vbuf[cur ^ 1];
+    ra.e_ba = kbuf[cur];
     ra.sum_hw = p.sum_hw; ra.C = p.C; ra.Ncam = p.Ncam; ra.Nscale = p.Nscale; ra.A = p.A; ra.P = p.P;
-    ra.G = p.G; ra.Cg = p.Cg; ra.rt = p.rt; ra.status = dev.status;
-    const int nteams = 8 * (32 / p.rt);
-    const long long rblocks = (nrows + nteams - 1) / nteams;
+    ra.G = p.G; ra.Cg = p.Cg; ra.rt = red_rt; ra.sbits = sbits; ra.status = dev.status;
+    ra.ncam = make_fastdiv((uint32_t)(p.Ncam > 0 ? p.Ncam : 1));
+    ra.pncam = make_fastdiv((uint32_t)((long long)p.P * p.Ncam > 0 ? (long long)p.P * p.Ncam : 1));
     const size_t smem = sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale;
-    if ((st = ensure_smem((const void*)red, smem, dev)) != MSDA_OK) return st;
-    red<<<(unsigned)rblocks, 256, smem, stream>>>(ra);
+    if (L.n > 0) {
+        if ((st = ensure_smem((const void*)det_prep_kernel, smem, dev)) != MSDA_OK) return st;
+        long long pb = ((long long)L.n + 255) / 256;
+        if (pb > (long long)dev.sm_count * 32) pb = (long long)dev.sm_count * 32;
+        det_prep_kernel<<<(unsigned)pb, 256, smem, stream>>>(ra, L.n, reinterpret_cast<float*>(kbuf[cur ^ 1]),
+                                                             vbuf[cur ^ 1], kbuf[cur]);
+        if ((st = check_launch("msda_backward prep")) != MSDA_OK) return st;
+    }
+    const int nteams = 8 * (32 / red_rt);
+    const long long rblocks = (nrows + nteams - 1) / nteams;
+    red<<<(unsigned)rblocks, 256, 0, stream>>>(ra);
     return check_launch("msda_backward reduce");
 }
 

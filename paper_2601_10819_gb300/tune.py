@@ -171,6 +171,8 @@ def main():
     ws = torch.empty(msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, False), dtype=torch.uint8, device=dev)
     tune_forward(T, out, workspace=fws, force=True)
     tune_backward(T, pr.grad_out, grads, workspace=ws, force=True)
+    dws = torch.empty(msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, True), dtype=torch.uint8, device=dev)
+    tune_backward(T, pr.grad_out, grads, deterministic=True, workspace=dws, force=True)
     scenes = [s.to(dev) for s in inputs.make_workload(4, with_grad=False)]
     tune_batched(scenes, force=True)
     with open(os.environ["MSDA_TUNE_CACHE"]) as f:
