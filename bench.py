@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -42,6 +43,15 @@ UNIT = "µs/frame"
 WORKLOAD = ("outside-in-64cam fwd+bwd: B1 Ncam64 maps 68x120/34x60/17x30/9x15 C256 G8 A900 P13, "
             "40% of (anchor,camera) pairs out of view, BF16 feat+weights, FP32 accumulate/out/grads, "
             "atomic backward")
+# Other workloads the step can run on (diagnostics and profiles; the benchmark line is the default one):
+# name -> (workload index, feature dtype, weight dtype, description)
+WORKLOADS = {
+    "outside-in-64cam": (2, None, None, WORKLOAD),
+    "train-16cam": (3, None, None, "train-16cam fwd+bwd: B4 Ncam16 maps 64x176/32x88/16x44/8x22 C256 G8 A900 P13, "
+                                   "BF16 feat, FP32 weights/accumulate/out/grads, atomic backward"),
+    "sparse4d-6cam-bf16": (1, "bf16", "bf16", "sparse4d-6cam fwd+bwd: B1 Ncam6 maps 64x176/32x88/16x44/8x22 C256 G8 "
+                                              "A900 P13, BF16 feat+weights, FP32 accumulate, atomic backward"),
+}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -65,6 +75,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="use the built-in launch mappings")
     ap.add_argument("--extras", action="store_true",
                     help="also time the fused occlusion-aware forward, the keypoint prologue and the half2 forward")
+    ap.add_argument("--workload", default="outside-in-64cam", choices=sorted(WORKLOADS),
+                    help="workload of the timed step (the benchmark line is quoted on outside-in-64cam)")
     ap.add_argument("--configs", action="store_true",
                     help="also time the 6-camera (FP32, BF16) and 16-camera training workloads")
     ap.add_argument("--with-batched", action="store_true",
@@ -223,12 +235,37 @@ def cpu_baseline(pr, sample_anchors):
     t1 = time.perf_counter()
     oracle.backward(*args, go)
     t2 = time.perf_counter()
+    oracle.forward(*args, nthreads=1)
+    t3 = time.perf_counter()
     A = pr.sampling_location.shape[1]
     na = sub.sampling_location.shape[1]
     per_frame_s = (t2 - t0) * A / na
     return {"value": per_frame_s * 1e6, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{na} of {A} anchors of one frame (fwd on {nthreads} OpenMP threads, bwd single-threaded), "
-                      f"fwd {t1 - t0:.2f} s + bwd {t2 - t1:.2f} s, scaled by {A}/{na}"}
+                      f"fwd {t1 - t0:.2f} s + bwd {t2 - t1:.2f} s, scaled by {A}/{na}",
+            "fwd_us_per_frame_all_cores": (t1 - t0) * A / na * 1e6,
+            "fwd_us_per_frame_1_core": (t3 - t2) * A / na * 1e6,
+            "bwd_us_per_frame_1_core": (t2 - t1) * A / na * 1e6,
+            "host": host_info()}
+
+
+def host_info():
+    """CPU model, logical CPUs and the CPUs this process may run on."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        affinity = len(os.sched_getaffinity(0))
+    except AttributeError:
+        affinity = os.cpu_count()
+    return {"cpu": model, "machine": platform.machine(), "nproc": os.cpu_count(), "affinity": affinity}
 
 
 def batched_serving(dev, stream, tune_it=True, reps=20):
@@ -358,7 +395,8 @@ def run_reference(args, rank, world):
     from paper_2601_10819_gb300 import inputs
     import oracle
     oracle.build()
-    pr = inputs.make_workload(2)
+    wl_idx, wl_f, wl_w, wl_desc = WORKLOADS[args.workload]
+    pr = inputs.make_workload(wl_idx, **({"feat_dtype": wl_f, "w_dtype": wl_w} if wl_f else {}))
     A = pr.sampling_location.shape[1]
     nthreads = oracle.max_threads()
     feat = oracle._f64(pr.feat)
@@ -383,7 +421,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v / 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+            "config": {"workload": wl_desc, "parallelism": "host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                              "sample": f"{na} anchors of {A} per step, scaled to a frame"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -413,7 +451,8 @@ def main():
         torch.distributed.barrier()
     msda.load()
 
-    pr = inputs.make_workload(2)
+    wl_idx, wl_f, wl_w, wl_desc = WORKLOADS[args.workload]
+    pr = inputs.make_workload(wl_idx, **({"feat_dtype": wl_f, "w_dtype": wl_w} if wl_f else {}))
     cnt = roofline.count(pr)
     d = pr.to(dev)
     B, sum_hw, C = d.feat.shape
@@ -491,6 +530,7 @@ def main():
     total_ms = start.elapsed_time(end)
     fwd_ms = sum(a.elapsed_time(b) for a, b, _ in evs) / args.steps
     bwd_ms = sum(b.elapsed_time(c) for _, b, c in evs) / args.steps
+    step_us = sorted(a.elapsed_time(c) * 1e3 for a, _, c in evs)
     total_ms, fwd_ms, bwd_ms = max_over_ranks([total_ms, fwd_ms, bwd_ms], dev)
     ms_per_step = total_ms / args.steps
     if msda.device_status() != 0:
@@ -555,6 +595,12 @@ def main():
     e2e_ms = max_over_ranks([s0.elapsed_time(s1) / args.e2e_steps], dev)[0]
 
     hbm_peak, peak_src = peaks()
+    feat_mb = d.feat.numel() * d.feat.element_size() / 1e6
+    gf_mb = gf.numel() * 4 / 1e6
+    l2_mb = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 126 << 20) / 1e6
+    l2_note = (f"inputs larger than L2 (feat {feat_mb:.0f} MB, grad_feat {gf_mb:.0f} MB per step, L2 {l2_mb:.0f} MB); "
+               f"no flush" if feat_mb + gf_mb > 2 * l2_mb else
+               f"inputs fit in L2 (feat {feat_mb:.0f} MB, grad_feat {gf_mb:.0f} MB): warm-cache timing")
     frames = world * B
     us_per_frame = ms_per_step * 1e3 / frames
     # dominant call and its roofline (algorithmic HBM bytes / measured duration)
@@ -576,16 +622,17 @@ def main():
         "metric": METRIC, "value": us_per_frame, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "accumulate": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": B, "parallelism": f"replicas x{world}",
+        "config": {"workload": wl_desc, "frames_per_step_per_gpu": B, "parallelism": f"replicas x{world}",
                    "backward": "deterministic" if det else "atomic",
                    "grad_feat_clear": None if det else {
                        "forward": "inside the forward kernel (msda_forward_train)",
                        "side": "torch fill on a side stream during the forward",
                        "inline": "memset inside msda_backward"}[args.clear],
-                   "l2": "inputs larger than L2 (feat 355 MB, grad_feat 710 MB per frame); no flush"},
+                   "l2": l2_note},
         "gsamples_per_s": cnt.nominal_samples * frames / (ms_per_step * 1e-3) / 1e9,
         "inview_gsamples_per_s": cnt.inview_samples * frames / (ms_per_step * 1e-3) / 1e9,
         "fwd_us": fwd_ms * 1e3, "bwd_us": bwd_ms * 1e3,
+        "step_us_p50": step_us[len(step_us) // 2], "step_us_p99": step_us[min(len(step_us) - 1, int(0.99 * len(step_us)))],
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes": dom_bytes},
