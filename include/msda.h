@@ -85,7 +85,12 @@ typedef struct {
                               kernel even with a workspace, 3 = FP16
                               features and weights accumulated in half2 (the
                               paper's plugin arithmetic, Sec. 5.3; less
-                              accurate); msda_backward (deterministic):
+                              accurate), 4 = the single-stage anchor kernel
+                              (every lane of a team locates its point-scales
+                              itself; by default a block locates each
+                              point-scale once into a shared list; also for
+                              msda_forward_train and _oae);
+                              msda_backward (deterministic):
                               2 = staged camera-group form                   */
     int vectors_per_lane;  /* 16-byte feature vectors per lane and corner row
                               (1, 2 or 4): more work per lane, fewer lanes

@@ -194,12 +194,14 @@ msda_status msda_forward(const void* feat, msda_dtype feat_dtype, const int32_t*
     if (!aligned16(out)) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: out must be 16-byte aligned");
     prefer_split(tuning, &p, 2);
     const bool half_acc = tuning && tuning->variant == 3;  // paper-faithful half2 accumulation
-    const bool direct = tuning && (tuning->variant == 1 || half_acc);  // force the anchor-per-block kernel
+    const bool direct = tuning && (tuning->variant == 1 || tuning->variant == 4 || half_acc);  // anchor kernel
     if (workspace && !direct && cg_supported(p)) {
         if (!aligned16(workspace)) return fail(MSDA_ERR_WORKSPACE, "msda_forward: workspace must be 16-byte aligned");
         return launch_forward_cg(p, out, out_dtype, workspace, workspace_bytes, (cudaStream_t)stream);
     }
-    return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream, nullptr, half_acc);
+    const bool units = !(tuning && tuning->variant == 4);  // variant 4: the single-stage anchor kernel
+    return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream, nullptr, half_acc, nullptr,
+                          units);
 }
 
 msda_status msda_forward_train(const void* feat, msda_dtype feat_dtype, const int32_t* spatial_shape,
@@ -221,8 +223,9 @@ msda_status msda_forward_train(const void* feat, msda_dtype feat_dtype, const in
     if (C % 4 != 0) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_train: C must be a multiple of 4");
     prefer_split(tuning, &p, 2);
     const bool half_acc = tuning && tuning->variant == 3;
+    const bool units = !(tuning && tuning->variant == 4);
     return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream, nullptr, half_acc,
-                          grad_feat);
+                          grad_feat, units);
 }
 
 msda_status msda_forward_oae(const void* feat, msda_dtype feat_dtype, const int32_t* spatial_shape,
@@ -242,8 +245,9 @@ msda_status msda_forward_oae(const void* feat, msda_dtype feat_dtype, const int3
     if (!aligned16(out) || !aligned16(visibility))
         return fail(MSDA_ERR_UNSUPPORTED, "msda_forward_oae: out and visibility must be 16-byte aligned");
     prefer_split(tuning, &p, 2);
+    const bool units = !(tuning && tuning->variant == 4);
     return launch_forward(p, out, out_dtype, pick_warps(tuning, 8), (cudaStream_t)stream,
-                          visibility ? visibility : nullptr);
+                          visibility ? visibility : nullptr, false, nullptr, units);
 }
 
 size_t msda_backward_workspace_size(int B, int sum_hw, int C, int Ncam, int Nscale, int A, int P, int G,

@@ -46,15 +46,18 @@ struct FwdArgs {
 };
 
 // Shared-memory carve-up of a forward block.
+// units: entries of the two-stage form's point-scale list (0 for the other forms).
 struct FwdSmem {
-    size_t maps, box, vn, loc, part, total;
-    __host__ __device__ FwdSmem(int nmaps, int P, int Ncam, int nteams, int C) {
+    size_t maps, box, vn, loc, part, list, total;
+    __host__ __device__ FwdSmem(int nmaps, int P, int Ncam, int nteams, int C, int units = 0) {
         maps = 0;
         box = align16(sizeof(MapInfo) * (size_t)nmaps);
         vn = box + sizeof(float4) * (size_t)Ncam;
         loc = vn + align16(sizeof(float) * (size_t)Ncam);
         part = loc + align16(sizeof(float2) * (size_t)P * Ncam);
-        total = part + sizeof(float) * (size_t)nteams * C;
+        list = part + align16(sizeof(float) * (size_t)nteams * C);
+        // UnitRec entries, their 2-byte list indices, the scan scratch
+        total = list + (units ? align16(26 * (size_t)units) + 64 : 0);
     }
 };
 
@@ -151,6 +154,170 @@ __device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, con
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two-stage form of accumulate_anchor (tuning variant 4).  The anchor's
+// point-scales (camera, keypoint, scale) are taken in chunks of
+// kUnitsPerThread per thread: stage A culls each one and locates its cell
+// once (instead of once in each of a team's lanes) and compacts the in-view
+// ones, in order, into a list in shared memory; stage B deals the list
+// round-robin to the teams, which only load and accumulate.  A team's sums run
+// in increasing point-scale order, so the result is deterministic; the
+// teams' shares differ from accumulate_anchor's, so the rounding does too.
+// ---------------------------------------------------------------------------
+constexpr int kUnitsPerThread = 4;
+
+struct UnitRec {
+    int row00;   // feature row of corner (y0, x0) inside the batch element (may be off the map: see the flags)
+    int W;       // map width: rows between y0 and y0 + 1
+    float fx, fy;
+    int wf;      // (index of the point-scale's weights) << 4 | vx0 | vx1 << 1 | vy0 << 2 | vy1 << 3
+    float scale; // camera factor of the fused occlusion-aware form, else 1
+};
+
+// Exclusive block-wide prefix sum (blockDim.x a multiple of 32); *total gets the sum.
+__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int t = wsum[w];
+            wsum[w] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    const int r = x - v + wsum[warp];
+    __syncthreads();  // wsum is reused by the next call
+    return r;
+}
+
+template <typename FT, typename WT, int NV>
+__device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ fb, const WT* __restrict__ wb,
+                                                        const MapInfo* __restrict__ smap,
+                                                        const float4* __restrict__ sbox,
+                                                        const float2* __restrict__ sloc, int C, int Ncam,
+                                                        int Nscale, int P, int G, int team, int nteams,
+                                                        float2* acc, const float* __restrict__ svn,
+                                                        UnitRec* srec, short* slist, int* sscan,
+                                                        const ZeroSlice* zs) {
+    constexpr int VEC = Elem<FT>::VEC;
+    const int per_cam = P * Nscale;
+    const int nunits = Ncam * per_cam;
+    const int chunk = blockDim.x * kUnitsPerThread;
+    const int nchunks = (nunits + chunk - 1) / chunk;
+    unsigned long long zpiece = 0;
+    if (zs) {
+        if (nchunks == 0) {  // nothing to carry the clearing: do it at once
+            for (unsigned long long j = zs->lo + threadIdx.x; j < zs->hi; j += blockDim.x)
+                __stcs(zs->ptr + j, make_uint4(0u, 0u, 0u, 0u));
+        } else {
+            zpiece = (zs->hi - zs->lo + nchunks - 1) / nchunks;
+        }
+    }
+    for (int ci = 0; ci < nchunks; ++ci) {
+        const int u0 = ci * chunk;
+        if (zs) {
+            const unsigned long long z0 = min(zs->lo + (unsigned long long)ci * zpiece, zs->hi);
+            const unsigned long long z1 = min(z0 + zpiece, zs->hi);
+            for (unsigned long long j = z0 + threadIdx.x; j < z1; j += blockDim.x)
+                __stcs(zs->ptr + j, make_uint4(0u, 0u, 0u, 0u));
+        }
+        // stage A: cull and locate this thread's kUnitsPerThread consecutive point-scales into its own entries
+        // of the record array, then list the in-view ones, in order, by index
+        const int mine = (int)threadIdx.x * kUnitsPerThread;
+        unsigned vmask = 0u;
+#pragma unroll
+        for (int i = 0; i < kUnitsPerThread; ++i) {
+            const int u = u0 + mine + i;
+            if (u < nunits) {
+                const int k = u / per_cam;
+                const int rem = u - k * per_cam;
+                const int pp = rem / Nscale;
+                const int sc = rem - pp * Nscale;
+                const float2 uv = sloc[pp * Ncam + k];
+                const float cs = svn ? svn[k] : 1.0f;
+                const MapInfo m = smap[k * Nscale + sc];
+                Cell c;
+                if (cs != 0.0f && in_box(uv, sbox[k]) && m.W != 0 && locate(uv.x, uv.y, m.H, m.W, c)) {
+                    UnitRec r;
+                    r.row00 = m.start + c.y0 * m.W + c.x0;
+                    r.W = m.W;
+                    r.fx = c.fx;
+                    r.fy = c.fy;
+                    r.wf = ((((pp * Ncam + k) * Nscale) + sc) << 4) | (c.x0 >= 0 ? 1 : 0) |
+                           (c.x0 + 1 < m.W ? 2 : 0) | (c.y0 >= 0 ? 4 : 0) | (c.y0 + 1 < m.H ? 8 : 0);
+                    r.scale = cs;
+                    srec[mine + i] = r;
+                    vmask |= 1u << i;
+                }
+            }
+        }
+        int off = block_excl_scan(__popc(vmask), sscan, sscan + 8);
+#pragma unroll
+        for (int i = 0; i < kUnitsPerThread; ++i)
+            if (vmask & (1u << i)) slist[off++] = (short)(mine + i);
+        __syncthreads();
+        const int total = sscan[8];
+        // stage B: the teams take the list round-robin
+        for (int q = team; q < total; q += nteams) {
+            const UnitRec r = srec[slist[q]];
+            const float wv = ldw(wb + (long long)(r.wf >> 4) * G) * r.scale;
+            const float ax = 1.0f - r.fx, ay = 1.0f - r.fy;
+            const float2 w00 = make_float2(wv * (ax * ay), wv * (ax * ay));
+            const float2 w01 = make_float2(wv * (r.fx * ay), wv * (r.fx * ay));
+            const float2 w10 = make_float2(wv * (ax * r.fy), wv * (ax * r.fy));
+            const float2 w11 = make_float2(wv * (r.fx * r.fy), wv * (r.fx * r.fy));
+            const FT* p00 = fb + (long long)r.row00 * C;
+            const FT* p10 = p00 + (long long)r.W * C;
+            uint4 q4[4][NV];
+            if ((r.wf & 15) == 15) {
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    q4[0][n] = ld16(p00 + n * VEC);
+                    q4[1][n] = ld16(p00 + C + n * VEC);
+                    q4[2][n] = ld16(p10 + n * VEC);
+                    q4[3][n] = ld16(p10 + C + n * VEC);
+                }
+            } else {
+                const bool vx0 = r.wf & 1, vx1 = r.wf & 2, vy0 = r.wf & 4, vy1 = r.wf & 8;
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int n = 0; n < NV; ++n) {
+                    q4[0][n] = (vy0 && vx0) ? ld16(p00 + n * VEC) : z;
+                    q4[1][n] = (vy0 && vx1) ? ld16(p00 + C + n * VEC) : z;
+                    q4[2][n] = (vy1 && vx0) ? ld16(p10 + n * VEC) : z;
+                    q4[3][n] = (vy1 && vx1) ? ld16(p10 + C + n * VEC) : z;
+                }
+            }
+#pragma unroll
+            for (int n = 0; n < NV; ++n) {
+                float2 f[4][VEC / 2];
+#pragma unroll
+                for (int cq = 0; cq < 4; ++cq) widen2(q4[cq][n], f[cq], FT());
+#pragma unroll
+                for (int j = 0; j < VEC / 2; ++j) {
+                    float2 a = acc[n * (VEC / 2) + j];
+                    a = __ffma2_rn(w00, f[0][j], a);
+                    a = __ffma2_rn(w01, f[1][j], a);
+                    a = __ffma2_rn(w10, f[2][j], a);
+                    a = __ffma2_rn(w11, f[3][j], a);
+                    acc[n * (VEC / 2) + j] = a;
+                }
+            }
+        }
+        __syncthreads();  // the list is rebuilt for the next chunk
+    }
+}
+
 // Sum the teams' partial rows in team order and write out[row] (n = C values).
 __device__ __forceinline__ void reduce_and_store(const float* spart, int nteams, int C, void* out,
                                                  int out_t, long long orow) {
@@ -171,14 +338,14 @@ __device__ __forceinline__ void reduce_and_store(const float* spart, int nteams,
 // shapes, every anchor's block is resident at once: then all blocks walk the
 // cameras in the same order together and each camera's maps are read from
 // HBM about once.
-template <typename FT, typename WT, int NV, bool CLEAR>
+template <typename FT, typename WT, int NV, bool CLEAR, bool UNITS>
 __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anchor_kernel(const FwdArgs p) {
     constexpr int CPL = Elem<FT>::VEC * NV;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nmaps = p.Ncam * p.Nscale;
     const int tpw = 32 / p.rt;
     const int nteams = (blockDim.x >> 5) * tpw;
-    const FwdSmem lay(nmaps, p.P, p.Ncam, nteams, p.C);
+    const FwdSmem lay(nmaps, p.P, p.Ncam, nteams, p.C, UNITS ? (int)blockDim.x * kUnitsPerThread : 0);
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
     float4* sbox = reinterpret_cast<float4*>(smem + lay.box);
     float* svn = reinterpret_cast<float*>(smem + lay.vn);
@@ -229,11 +396,31 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
             s_zs.chunk = (s_zs.hi - s_zs.lo + nitems - 1) / nitems;
         }
         __syncthreads();
-        accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc,
-                                      p.vis ? svn : nullptr, &s_zs, lane & (p.rt - 1), p.rt);
+        if constexpr (UNITS)
+            accumulate_anchor_units<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team,
+                                                nteams, acc, p.vis ? svn : nullptr,
+                                                reinterpret_cast<UnitRec*>(smem + lay.list),
+                                                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x *
+                                                                                       kUnitsPerThread),
+                                                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
+                                                                                                 kUnitsPerThread)),
+                                                &s_zs);
+        else
+            accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
+                                          acc, p.vis ? svn : nullptr, &s_zs, lane & (p.rt - 1), p.rt);
     } else {
-        accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams, acc,
-                                      p.vis ? svn : nullptr);
+        if constexpr (UNITS)
+            accumulate_anchor_units<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team,
+                                                nteams, acc, p.vis ? svn : nullptr,
+                                                reinterpret_cast<UnitRec*>(smem + lay.list),
+                                                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x *
+                                                                                       kUnitsPerThread),
+                                                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
+                                                                                                 kUnitsPerThread)),
+                                                nullptr);
+        else
+            accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
+                                          acc, p.vis ? svn : nullptr);
     }
 
     float* mine = spart + (size_t)team * p.C + c0;
@@ -366,7 +553,7 @@ __global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tpw = 32 / p.rt;
     const int nteams = (blockDim.x >> 5) * tpw;
-    const FwdSmem lay(p.max_ncam * p.Nscale, p.P, p.max_ncam, nteams, p.C);
+    const FwdSmem lay(p.max_ncam * p.Nscale, p.P, p.max_ncam, nteams, p.C, (int)blockDim.x * kUnitsPerThread);
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem + lay.maps);
     float4* sbox = reinterpret_cast<float4*>(smem + lay.box);
     float2* sloc = reinterpret_cast<float2*>(smem + lay.loc);
@@ -420,7 +607,11 @@ __global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
             float2 acc[CPL / 2];
 #pragma unroll
             for (int j = 0; j < CPL / 2; ++j) acc[j] = make_float2(0.0f, 0.0f);
-            accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc);
+            accumulate_anchor_units<FT, WT, NV>(
+                fb, wb, smap, sbox, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc, nullptr,
+                reinterpret_cast<UnitRec*>(smem + lay.list),
+                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x * kUnitsPerThread),
+                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x * kUnitsPerThread)), nullptr);
             float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
             for (int j = 0; j < CPL / 2; j += 2)
@@ -444,12 +635,12 @@ __global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
 using FwdKernel = void (*)(const FwdArgs);
 using BatchedKernel = void (*)(const BatchedArgs);
 
-template <typename FT, typename WT, bool CLEAR>
+template <typename FT, typename WT, bool CLEAR, bool UNITS>
 static FwdKernel fwd_pick_nv(int nv) {
     switch (nv) {
-        case 1: return fwd_anchor_kernel<FT, WT, 1, CLEAR>;
-        case 2: return fwd_anchor_kernel<FT, WT, 2, CLEAR>;
-        case 4: return fwd_anchor_kernel<FT, WT, 4, CLEAR>;
+        case 1: return fwd_anchor_kernel<FT, WT, 1, CLEAR, UNITS>;
+        case 2: return fwd_anchor_kernel<FT, WT, 2, CLEAR, UNITS>;
+        case 4: return fwd_anchor_kernel<FT, WT, 4, CLEAR, UNITS>;
     }
     return nullptr;
 }
@@ -465,13 +656,13 @@ static BatchedKernel batched_pick_nv(int nv) {
 }
 
 // Supported (feature, weight) dtype pairs: weights in FP32 or in the feature dtype.
-template <bool CLEAR>
+template <bool CLEAR, bool UNITS>
 static FwdKernel fwd_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
-    if (ft == MSDA_F32 && wt == MSDA_F32) return fwd_pick_nv<float, float, CLEAR>(nv);
-    if (ft == MSDA_BF16 && wt == MSDA_BF16) return fwd_pick_nv<__nv_bfloat16, __nv_bfloat16, CLEAR>(nv);
-    if (ft == MSDA_BF16 && wt == MSDA_F32) return fwd_pick_nv<__nv_bfloat16, float, CLEAR>(nv);
-    if (ft == MSDA_F16 && wt == MSDA_F16) return fwd_pick_nv<__half, __half, CLEAR>(nv);
-    if (ft == MSDA_F16 && wt == MSDA_F32) return fwd_pick_nv<__half, float, CLEAR>(nv);
+    if (ft == MSDA_F32 && wt == MSDA_F32) return fwd_pick_nv<float, float, CLEAR, UNITS>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_BF16) return fwd_pick_nv<__nv_bfloat16, __nv_bfloat16, CLEAR, UNITS>(nv);
+    if (ft == MSDA_BF16 && wt == MSDA_F32) return fwd_pick_nv<__nv_bfloat16, float, CLEAR, UNITS>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F16) return fwd_pick_nv<__half, __half, CLEAR, UNITS>(nv);
+    if (ft == MSDA_F16 && wt == MSDA_F32) return fwd_pick_nv<__half, float, CLEAR, UNITS>(nv);
     return nullptr;
 }
 
@@ -485,7 +676,7 @@ static BatchedKernel batched_kernel_for(msda_dtype ft, msda_dtype wt, int nv) {
 }
 
 msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int warps,
-                           cudaStream_t stream, const float* vis, bool half_acc, float* clear) {
+                           cudaStream_t stream, const float* vis, bool half_acc, float* clear, bool units) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);
     if (st != MSDA_OK) return st;
@@ -500,13 +691,17 @@ msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int wa
         clear = nullptr;
     }
     // the clearing kernel is chosen only when `clear` is still set, so its slice pointer is never NULL
-    FwdKernel k = clear ? fwd_kernel_for<true>(p.feat_t, p.w_t, p.nv) : fwd_kernel_for<false>(p.feat_t, p.w_t, p.nv);
+    if ((long long)p.Ncam * p.P * p.Nscale >= (1ll << 26)) units = false;  // the unit index is a 32-bit int
+    FwdKernel k = clear ? (units ? fwd_kernel_for<true, true>(p.feat_t, p.w_t, p.nv)
+                                 : fwd_kernel_for<true, false>(p.feat_t, p.w_t, p.nv))
+                        : (units ? fwd_kernel_for<false, true>(p.feat_t, p.w_t, p.nv)
+                                 : fwd_kernel_for<false, false>(p.feat_t, p.w_t, p.nv));
     if (half_acc) k = p.nv == 1 ? fwd_anchor_h2_kernel<1> : p.nv == 2 ? fwd_anchor_h2_kernel<2> : fwd_anchor_h2_kernel<4>;
     if (!k) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: unsupported feature/weight dtype pair");
     if (nblocks == 0) return MSDA_OK;
     if (nblocks > 0x7fffffffLL) return fail(MSDA_ERR_UNSUPPORTED, "msda_forward: B*A too large");
     const int nteams = warps * (32 / p.rt);
-    const FwdSmem lay(p.Ncam * p.Nscale, p.P, p.Ncam, nteams, p.C);
+    const FwdSmem lay(p.Ncam * p.Nscale, p.P, p.Ncam, nteams, p.C, units && !half_acc ? warps * 32 * kUnitsPerThread : 0);
     st = ensure_smem((const void*)k, lay.total, dev);
     if (st != MSDA_OK) return st;
     FwdArgs a;
@@ -539,7 +734,7 @@ msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int
     if (!ws || ws_bytes < need)
         return fail(MSDA_ERR_WORKSPACE, "msda_forward_batched: workspace needs %zu bytes", need);
     const int nteams = warps * (32 / rt);
-    const FwdSmem lay(max_ncam * Nscale, P, max_ncam, nteams, C);
+    const FwdSmem lay(max_ncam * Nscale, P, max_ncam, nteams, C, warps * 32 * kUnitsPerThread);
     st = ensure_smem((const void*)k, lay.total, dev);
     if (st != MSDA_OK) return st;
     if (cudaMemsetAsync(ws, 0, need, stream) != cudaSuccess) return check_launch("msda_forward_batched memset");

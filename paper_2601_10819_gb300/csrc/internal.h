@@ -55,7 +55,7 @@ int dtype_size(msda_dtype t);
 // into a grad_feat the caller already cleared.
 msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int warps,
                            cudaStream_t stream, const float* vis = nullptr, bool half_acc = false,
-                           float* clear = nullptr);
+                           float* clear = nullptr, bool units = false);
 msda_status launch_backward_atomic(const Problem& p, const float* grad_out, float* grad_feat,
                                    float* grad_loc, float* grad_w, void* ws, size_t ws_bytes, int warps,
                                    bool zeroed, cudaStream_t stream);

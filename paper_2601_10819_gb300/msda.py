@@ -214,7 +214,7 @@ def forward_train(feat, spatial_shape, scale_start_index, sampling_location, wei
 
 def forward_oae(feat, spatial_shape, scale_start_index, sampling_location, weights, visibility, *,
                 out: Optional[torch.Tensor] = None, out_dtype: torch.dtype = torch.float32,
-                warps: Optional[int] = None, vec: int = 0) -> torch.Tensor:
+                warps: Optional[int] = None, vec: int = 0, variant: int = 0) -> torch.Tensor:
     """msda_forward_oae: the operator fused with the visibility-weighted mean over cameras."""
     lib = load()
     B, sum_hw, C, Ncam, Nscale, A, P, G = _dims(feat, spatial_shape, scale_start_index, sampling_location, weights)
@@ -226,7 +226,7 @@ def forward_oae(feat, spatial_shape, scale_start_index, sampling_location, weigh
     rc = lib.msda_forward_oae(_ptr(feat), _DT[feat.dtype], _ptr(spatial_shape), _ptr(scale_start_index),
                               _ptr(sampling_location), _ptr(weights), _DT[weights.dtype], _ptr(visibility),
                               _ptr(out), _DT[out.dtype], B, sum_hw, C, Ncam, Nscale, A, P, G,
-                              _tuning(warps, None, 0, vec), ctypes.c_void_p(_stream(feat.device)))
+                              _tuning(warps, None, variant, vec), ctypes.c_void_p(_stream(feat.device)))
     _check("msda_forward_oae", rc)
     return out
 

@@ -4,7 +4,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import (TOL_FP32, TOL_LOWP_OUT, ensure_lib, gpu_forward, oracle_forward, relerr)
+from gpu_util import (TOL_FP32, TOL_LOWP_OUT, ensure_lib, gpu_forward, is_lowp, oracle_forward, relerr)
 from paper_2601_10819_gb300 import inputs, msda
 
 pytestmark = pytest.mark.gpu
@@ -205,3 +205,52 @@ def test_staged_and_anchor_kernels_agree():
     a = gpu_forward(pr).cpu().double().numpy()
     b = gpu_forward(pr, workspace=None).cpu().double().numpy()
     assert relerr(a, b) <= 1e-6
+
+
+@pytest.mark.parametrize("wl,fdt,wdt", [(0, None, None), (1, "f32", "f32"), (1, "bf16", "bf16"), (1, "f16", "f32"),
+                                        (2, None, None), (3, None, None)])
+@pytest.mark.parametrize("vec", [1, 2, 4])
+def test_two_stage_and_single_stage_forwards(wl, fdt, wdt, vec):
+    """The default two-stage forward (each chunk of point-scales culled and located once into a shared-memory
+    list that the teams share out) and the single-stage one (variant 4, every lane locates its own
+    point-scales): both equal to the oracle, equal to each other within FP32 rounding, bitwise stable."""
+    kw = dict(feat_dtype=fdt, w_dtype=wdt) if fdt else {}
+    pr = inputs.make_workload(wl, with_grad=False, **kw)
+    if wl >= 2:
+        pr = pr.anchors(range(120))
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    ref = oracle_forward(pr)
+    for warps in (1, 2, 8):
+        got = msda.forward(*T, warps=warps, vec=vec, variant=4)
+        again = msda.forward(*T, warps=warps, vec=vec, variant=4)
+        plain = msda.forward(*T, warps=warps, vec=vec)
+        torch.cuda.synchronize()
+        assert torch.equal(got, again)
+        assert relerr(got.cpu().double().numpy(), plain.cpu().double().numpy()) <= TOL_FP32  # another sum order
+        err = relerr(got.cpu().double().numpy(), ref)
+        assert err <= (TOL_LOWP_OUT if is_lowp(pr) else TOL_FP32), (warps, err)
+    assert msda.device_status() == 0
+
+
+def test_single_stage_forward_edge_cases():
+    """NaN and far points, boundary cells, maps of one pixel, no anchors, no points (variant 4; the default form
+    meets the same cases in the tests above)."""
+    gen = torch.Generator().manual_seed(21)
+    pr = inputs.make_problem(gen, B=2, cam_maps=[[(5, 7), (3, 2), (1, 1)]] * 3, C=64, G=4, A=9, P=5,
+                             loc_range=(-0.3, 1.3))
+    loc = pr.sampling_location.clone()
+    loc[0, 0, 0, 0] = float("nan")
+    loc[1, 2, 1, 1] = torch.tensor([1e9, -1e9])
+    loc[0, 3, 2, 2] = torch.tensor([0.0, 1.0])
+    pr = inputs.Problem(pr.feat, pr.spatial_shape, pr.scale_start_index, loc.contiguous(), pr.weights, None)
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    for warps in (1, 4):
+        got = msda.forward(*T, variant=4, warps=warps)
+        assert relerr(got.cpu().double().numpy(), oracle_forward(pr)) <= TOL_FP32
+    for A, P in ((0, 2), (3, 0)):
+        e = inputs.make_problem(gen, B=1, cam_maps=[[(4, 4)]], C=32, G=4, A=A, P=P).to("cuda")
+        out = msda.forward(e.feat, e.spatial_shape, e.scale_start_index, e.sampling_location, e.weights, variant=4)
+        assert out.shape == (1, A, 32) and (out.numel() == 0 or torch.all(out == 0))
+    assert msda.device_status() == 0

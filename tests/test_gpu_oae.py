@@ -58,3 +58,13 @@ def test_zero_visibility_anchor_is_zero_and_one_hot_selects_camera():
     assert np.all(got[0, 3] == 0.0)
     ref = oracle.forward_oae(*pr.tensors(), vis)
     assert relerr(got, ref) <= TOL_FP32
+
+
+def test_single_stage_fused_fusion_matches_the_default_form():
+    pr = inputs.make_workload(2, with_grad=False).anchors(range(100))
+    vis = inputs.make_visibility(pr, 3).to("cuda")
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    a = msda.forward_oae(*T, vis)
+    b = msda.forward_oae(*T, vis, variant=4)
+    assert relerr(b.cpu().double().numpy(), a.cpu().double().numpy()) <= TOL_FP32  # another FP32 sum order
