@@ -4,7 +4,8 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import (TOL_FP32, TOL_LOWP_GRAD, ensure_lib, is_lowp, oracle_backward, relerr)
+from gpu_util import (TOL_FP32, TOL_LOWP_GRAD, TOL_LOWP_OUT, ensure_lib, is_lowp, oracle_backward, oracle_forward,
+                      relerr)
 from paper_2601_10819_gb300 import inputs, msda
 
 pytestmark = pytest.mark.gpu
@@ -333,4 +334,34 @@ def test_forward_train_clears_grad_feat_and_matches_forward(case):
         g = [t.cpu() for t in msda.backward(*T, d.grad_out, grads=(gf, gl, gw), grad_feat_zeroed=True)]
         assert relerr(g[0].double().numpy(), refg[0].double().numpy()) <= 1e-6
         assert torch.equal(g[1], refg[1]) and torch.equal(g[2], refg[2])
+    assert msda.device_status() == 0
+
+
+def test_bench_step_in_its_launch_configuration_full_size():
+    """The timed step of bench.py exactly as it runs (the shipped GB300 mappings, msda_forward_train clearing
+    grad_feat, then the atomic backward with the zeroed flag) on the full 64-camera frame, against the oracle."""
+    import json
+    import os
+    from paper_2601_10819_gb300 import tune
+    pr = inputs.make_workload(2)
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    table = json.load(open(tune.SHIPPED))
+    pick = lambda kind: next((v["best"] for k, v in table.items() if f"|{kind}|" in k and "hw694080" in k), {})
+    ft, bt = pick("fwd"), pick("bwd")
+    B, sum_hw, C = d.feat.shape
+    gf = torch.full((B, sum_hw, C), float("nan"), device="cuda")
+    gl, gw = torch.empty(d.sampling_location.shape, device="cuda"), torch.empty(d.weights.shape, device="cuda")
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+    for _ in range(2):  # a second step over the first one's gradients
+        out = msda.forward_train(*T, gf, warps=ft.get("warps") or None, vec=ft.get("vec", 0))
+        msda.backward(*T, d.grad_out, workspace=ws, grads=(gf, gl, gw), warps=bt.get("warps") or None,
+                      vec=bt.get("vec", 0), grad_feat_zeroed=True)
+    torch.cuda.synchronize()
+    assert relerr(out.cpu().double().numpy(), oracle_forward(pr)) <= TOL_LOWP_OUT
+    ref = oracle_backward(pr)
+    for g, r, name in zip((gf, gl, gw), ref, ["dfeat", "dloc", "dw"]):
+        e = relerr(g.cpu().double().numpy(), r)
+        print(f"bench step {name} rel err {e:.2e}")
+        assert e <= TOL_LOWP_GRAD
     assert msda.device_status() == 0

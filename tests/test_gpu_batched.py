@@ -95,3 +95,28 @@ def test_bad_descriptor_is_reported_not_faulted():
     plan.run()
     torch.cuda.synchronize()
     assert msda.device_status() == 5
+
+
+def test_full_serving_batch_in_its_launch_configuration_sampled():
+    """The 16-scene serving batch of bench.py (762 cameras, 14 161 anchors) with the shipped GB300 mapping,
+    checked against the oracle on 12 anchors per scene (first, last and spread between)."""
+    import json
+    from paper_2601_10819_gb300 import tune
+    scenes_cpu = inputs.make_workload(4, with_grad=False)
+    scenes = [s.to("cuda") for s in scenes_cpu]
+    table = json.load(open(tune.SHIPPED))
+    cfg = next((v["best"] for k, v in table.items() if "|batched|" in k), {})
+    plan = msda.plan_batched(scenes, warps=cfg.get("warps") or None, blocks_per_sm=cfg.get("bps") or None,
+                             vec=cfg.get("vec", 0))
+    outs = plan.run()
+    torch.cuda.synchronize()
+    worst = 0.0
+    for s, o in zip(scenes_cpu, outs):
+        A = s.sampling_location.shape[1]
+        idx = sorted(set(np.linspace(0, A - 1, 12).round().astype(int).tolist()))
+        ref = oracle_forward(s.anchors(idx))
+        got = o.cpu()[idx].double().numpy()[None]
+        worst = max(worst, relerr(got, ref))
+    print(f"full serving batch, sampled anchors: rel err {worst:.2e}")
+    assert worst <= TOL_LOWP_OUT
+    assert msda.device_status() == 0
