@@ -3,9 +3,10 @@
 // The feature gradient is a scatter: every in-bound corner of every sampled
 // point adds w_g * omega * go[c] to one feature row.  Scattering with
 // atomics makes the FP32 summation order depend on timing.  This mode
-// instead gathers: it builds, for every corner of every point-scale, the
-// key (feature row) and the value (the corner's slot id), sorts the pairs by
-// key with a stable LSD radix sort, so that equal rows keep the slot order,
+// instead gathers: it builds, for every in-bound corner of every
+// point-scale, the key (feature row) and the value (the corner's slot id),
+// compacted in slot order, sorts the pairs by key with a stable LSD radix
+// sort, so that equal rows keep the slot order,
 // turns the sorted slots into flat (omega, point-scale, anchor row) arrays,
 // and then lets one team per feature row sum its contributions in that
 // order and write the row once (rows nobody touches get zeros, so no memset
@@ -25,13 +26,16 @@ namespace msda {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kTile = kSortThreads * kSortItems;  // keys per sort block
+constexpr int kKeyPts = 4;                         // point-scales per thread in the key kernels
+constexpr int kKeyBlock = 256 * kKeyPts;           // point-scales per key block
 
 struct DetLayout {
     size_t n;       // slots: 4 per point-scale
     size_t nrows;   // B * sum_hw
     int nb;         // sort tiles
     int passes;     // 8-bit digit passes
-    size_t k0, v0, k1, v1, hist, tot, rowptr, total;
+    size_t k0, v0, k1, v1, hist, tot, rowptr, cnt, nvalid, total;
+    int nkb;        // key blocks
 };
 
 static DetLayout det_layout(long long npts, long long nrows) {
@@ -51,6 +55,9 @@ static DetLayout det_layout(long long npts, long long nrows) {
     L.hist = take(4 * (size_t)256 * (L.nb > 0 ? L.nb : 1));
     L.tot = take(4 * 256);
     L.rowptr = take(4 * (L.nrows + 1));
+    L.nkb = (int)((npts + kKeyBlock - 1) / kKeyBlock);
+    L.cnt = take(4 * (size_t)(L.nkb > 0 ? L.nkb : 1));
+    L.nvalid = take(4);
     L.total = off;
     return L;
 }
@@ -71,7 +78,7 @@ struct KeyArgs {
     uint32_t* vals;
     long long npts;
     int sum_hw, A, P, Ncam, Nscale, sbits;
-    uint32_t sentinel;
+    uint32_t* counts;  // per key block: in-bound corners (count pass), then their exclusive prefix (write pass)
     int* status;
 };
 
@@ -98,48 +105,6 @@ static int scale_bits(int Nscale) {
     int b = 0;
     while ((1 << b) < Nscale) ++b;
     return b;
-}
-
-__global__ void __launch_bounds__(256) det_keys_kernel(const KeyArgs a) {
-    for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < a.npts;
-         pt += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(pt % a.Nscale);
-        const long long t = pt / a.Nscale;            // ((b*A + a)*P + p)*Ncam + k
-        const int k = (int)(t % a.Ncam);
-        const long long b = t / ((long long)a.Ncam * a.P * a.A);
-        const MapInfo m = load_map(a.shape, a.start, k * a.Nscale + s, a.sum_hw, a.status);
-        const float2 uv = __ldg(reinterpret_cast<const float2*>(a.loc) + t);
-        Cell c;
-        const bool in = (m.W != 0) && locate(uv.x, uv.y, m.H, m.W, c);
-        uint32_t key[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = c.y0 + (q >> 1), j = c.x0 + (q & 1);
-            const bool ok = in && i >= 0 && i < m.H && j >= 0 && j < m.W;
-            key[q] = ok ? (uint32_t)(b * a.sum_hw + m.start + i * m.W + j) : a.sentinel;
-        }
-        const uint32_t slot = (((uint32_t)t << a.sbits) | (uint32_t)s) << 2;
-        reinterpret_cast<uint4*>(a.keys)[pt] = make_uint4(key[0], key[1], key[2], key[3]);
-        reinterpret_cast<uint4*>(a.vals)[pt] = make_uint4(slot, slot + 1, slot + 2, slot + 3);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// 2. Stable LSD radix sort, 8-bit digits: histogram, per-digit scan, scatter
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t* __restrict__ keys, size_t n,
-                                                                  int shift, uint32_t* __restrict__ hist, int nb) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const size_t base = (size_t)blockIdx.x * kTile;
-#pragma unroll 4
-    for (int r = 0; r < kSortItems; ++r) {
-        const size_t i = base + (size_t)r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(__ldg(keys + i) >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
 // Inclusive scan of one value per thread over a block of 32*W threads.
@@ -169,6 +134,89 @@ __device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* w
     return r;
 }
 
+// Keys of the in-bound corners of one point-scale; bit q of the result marks corner q in bounds.
+__device__ __forceinline__ unsigned corner_keys(const KeyArgs& a, long long pt, uint32_t key[4]) {
+    const int s = (int)(pt % a.Nscale);
+    const long long t = pt / a.Nscale;            // ((b*A + a)*P + p)*Ncam + k
+    const int k = (int)(t % a.Ncam);
+    const long long b = t / ((long long)a.Ncam * a.P * a.A);
+    const MapInfo m = load_map(a.shape, a.start, k * a.Nscale + s, a.sum_hw, a.status);
+    const float2 uv = __ldg(reinterpret_cast<const float2*>(a.loc) + t);
+    Cell c;
+    const bool in = (m.W != 0) && locate(uv.x, uv.y, m.H, m.W, c);
+    unsigned mask = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = c.y0 + (q >> 1), j = c.x0 + (q & 1);
+        const bool ok = in && i >= 0 && i < m.H && j >= 0 && j < m.W;
+        key[q] = ok ? (uint32_t)(b * a.sum_hw + m.start + i * m.W + j) : 0u;
+        mask |= ok ? (1u << q) : 0u;
+    }
+    return mask;
+}
+
+// Block b handles point-scales [b*kKeyBlock, (b+1)*kKeyBlock), kKeyPts consecutive ones per thread.  The count
+// pass stores the block's number of in-bound corners; the write pass stores only those corners' (key, slot)
+// pairs, at the block's prefix plus the thread's prefix inside the block, so the pairs stay in slot order
+// (which the stable sort keeps for equal keys) and the sort sees no out-of-bounds corners at all.
+template <bool WRITE>
+__global__ void __launch_bounds__(256) det_keys_kernel(const KeyArgs a) {
+    __shared__ uint32_t ws[32];
+    const long long base = (long long)blockIdx.x * kKeyBlock + (long long)threadIdx.x * kKeyPts;
+    uint32_t key[kKeyPts][4];
+    unsigned mask[kKeyPts];
+    uint32_t cnt = 0u;
+#pragma unroll
+    for (int i = 0; i < kKeyPts; ++i) {
+        mask[i] = (base + i < a.npts) ? corner_keys(a, base + i, key[i]) : 0u;
+        cnt += (uint32_t)__popc(mask[i]);
+    }
+    uint32_t total;
+    const uint32_t incl = block_inclusive_scan<8>(cnt, ws, &total);
+    if (!WRITE) {
+        if (threadIdx.x == 0) a.counts[blockIdx.x] = total;
+        return;
+    }
+    uint32_t off = a.counts[blockIdx.x] + incl - cnt;
+#pragma unroll
+    for (int i = 0; i < kKeyPts; ++i) {
+        const long long pt = base + i;
+        const uint32_t slot = ((((uint32_t)(pt / a.Nscale)) << a.sbits) | (uint32_t)(pt % a.Nscale)) << 2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (mask[i] & (1u << q)) {
+                a.keys[off] = key[i][q];
+                a.vals[off] = slot + (uint32_t)q;
+                ++off;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Stable LSD radix sort, 8-bit digits: histogram, per-digit scan, scatter
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
+                                                                  const uint32_t* __restrict__ n_dev, int shift,
+                                                                  uint32_t* __restrict__ hist, int nb) {
+    const size_t n = *n_dev;  // keys to sort (the grid covers the most there can be)
+    const size_t base = (size_t)blockIdx.x * kTile;
+    if (base >= n) {  // a tile past the keys: empty counts (uniform over the block)
+        hist[(size_t)threadIdx.x * nb + blockIdx.x] = 0u;
+        return;
+    }
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < kSortItems; ++r) {
+        const size_t i = base + (size_t)r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(__ldg(keys + i) >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
 // Block d turns hist[d][0..nb) into exclusive prefixes and writes totals[d].
 __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ hist, int nb,
                                                           uint32_t* __restrict__ totals) {
@@ -188,8 +236,10 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__
 
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, size_t n, int shift, const uint32_t* __restrict__ hist,
+    uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ hist,
     const uint32_t* __restrict__ totals, int nb) {
+    const size_t n = *n_dev;
+    if ((size_t)blockIdx.x * kTile >= n) return;  // a tile past the keys (uniform over the block)
     constexpr int NW = kSortThreads / 32;
     __shared__ uint32_t base[256];
     __shared__ uint32_t wcnt[NW][256];
@@ -234,8 +284,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
 }
 
 // rowptr[r] = number of sorted keys < r, for r in [0, nrows].
-__global__ void __launch_bounds__(256) row_ptr_kernel(const uint32_t* __restrict__ ks, size_t n,
-                                                      uint32_t nrows, uint32_t* __restrict__ rowptr) {
+__global__ void __launch_bounds__(256) row_ptr_kernel(const uint32_t* __restrict__ ks,
+                                                      const uint32_t* __restrict__ n_dev, uint32_t nrows,
+                                                      uint32_t* __restrict__ rowptr) {
+    const size_t n = *n_dev;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i <= n; i += (size_t)gridDim.x * blockDim.x) {
         const unsigned long long lo = (i == 0) ? 0ull : (unsigned long long)ks[i - 1] + 1ull;
         unsigned long long hi = (i == n) ? (unsigned long long)nrows : (unsigned long long)ks[i];
@@ -276,7 +328,7 @@ __global__ void __launch_bounds__(256) det_prep_kernel(RedArgs a, size_t n, floa
     for (int i = threadIdx.x; i < nmaps; i += blockDim.x)
         smap[i] = load_map(a.shape, a.start, i, a.sum_hw, nullptr);
     __syncthreads();
-    const size_t nvalid = a.rowptr[a.nrows];  // the sentinel keys sort after every row
+    const size_t nvalid = a.rowptr[a.nrows];  // every sorted key is an in-bound corner
     const uint32_t smask = (1u << a.sbits) - 1u;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nvalid && e < n;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -399,21 +451,25 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     uint32_t* tot = reinterpret_cast<uint32_t*>(base + L.tot);
     uint32_t* rowptr = reinterpret_cast<uint32_t*>(base + L.rowptr);
     int cur = 0;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.cnt);
+    uint32_t* nvalid = reinterpret_cast<uint32_t*>(base + L.nvalid);
+    if (cudaMemsetAsync(nvalid, 0, sizeof(uint32_t), stream) != cudaSuccess) return check_launch("msda_backward");
     if (npts > 0) {
         KeyArgs ka;
         ka.shape = p.shape; ka.start = p.start; ka.loc = p.loc; ka.keys = kbuf[0]; ka.vals = vbuf[0];
         ka.npts = npts; ka.sum_hw = p.sum_hw; ka.A = p.A; ka.P = p.P; ka.Ncam = p.Ncam;
-        ka.Nscale = p.Nscale; ka.sbits = sbits; ka.sentinel = (uint32_t)nrows; ka.status = dev.status;
-        long long kb = (npts + 255) / 256;
-        if (kb > (long long)dev.sm_count * 64) kb = (long long)dev.sm_count * 64;
-        det_keys_kernel<<<(unsigned)kb, 256, 0, stream>>>(ka);
+        ka.Nscale = p.Nscale; ka.sbits = sbits; ka.counts = counts; ka.status = dev.status;
+        // in-bound corners per key block, their prefix (and total), then the compacted (key, slot) pairs
+        det_keys_kernel<false><<<L.nkb, 256, 0, stream>>>(ka);
+        radix_scan_kernel<<<1, 1024, 0, stream>>>(counts, L.nkb, nvalid);
+        det_keys_kernel<true><<<L.nkb, 256, 0, stream>>>(ka);
         if ((st = check_launch("msda_backward keys")) != MSDA_OK) return st;
         for (int pass = 0; pass < L.passes; ++pass) {
             const int shift = 8 * pass;
-            radix_hist_kernel<<<L.nb, kSortThreads, 0, stream>>>(kbuf[cur], L.n, shift, hist, L.nb);
+            radix_hist_kernel<<<L.nb, kSortThreads, 0, stream>>>(kbuf[cur], nvalid, shift, hist, L.nb);
             radix_scan_kernel<<<256, 1024, 0, stream>>>(hist, L.nb, tot);
             radix_scatter_kernel<<<L.nb, kSortThreads, 0, stream>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1],
-                                                                    vbuf[cur ^ 1], L.n, shift, hist, tot, L.nb);
+                                                                    vbuf[cur ^ 1], nvalid, shift, hist, tot, L.nb);
             if ((st = check_launch("msda_backward sort")) != MSDA_OK) return st;
             cur ^= 1;
         }
@@ -421,7 +477,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     {
         long long rb = ((long long)L.n + 1 + 255) / 256;
         if (rb > (long long)dev.sm_count * 32) rb = (long long)dev.sm_count * 32;
-        row_ptr_kernel<<<(unsigned)rb, 256, 0, stream>>>(kbuf[cur], L.n, (uint32_t)nrows, rowptr);
+        row_ptr_kernel<<<(unsigned)rb, 256, 0, stream>>>(kbuf[cur], nvalid, (uint32_t)nrows, rowptr);
         if ((st = check_launch("msda_backward row offsets")) != MSDA_OK) return st;
     }
     RedArgs ra;
