@@ -38,6 +38,7 @@ struct BwdArgs {
     int B, sum_hw, C, Ncam, Nscale, A, P, G, Cg;
     int rt;
     int scatter;  // 0: skip the feature-gradient atomics (deterministic mode); 1, 2: scatter
+    int wide;     // a lane's two 16-byte chunks are 32-byte aligned: one 256-bit load
     unsigned long long* counter;  // next unhanded item (dynamic order) or NULL (static stride)
     int* status;
 };
@@ -134,7 +135,12 @@ __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
                 const long long rW = (long long)m.W * p.C;
                 const FT* p00 = fb + r00;
                 uint4 q[4][NV];
-                if (vx0 && vx1 && vy0 && vy1) {
+                if (NV == 2 && p.wide && vx0 && vx1 && vy0 && vy1) {
+                    ld32(p00, q[0][0], q[0][NV - 1]);
+                    ld32(p00 + p.C, q[1][0], q[1][NV - 1]);
+                    ld32(p00 + rW, q[2][0], q[2][NV - 1]);
+                    ld32(p00 + rW + p.C, q[3][0], q[3][NV - 1]);
+                } else if (vx0 && vx1 && vy0 && vy1) {
 #pragma unroll
                     for (int n = 0; n < NV; ++n) {
                         q[0][n] = ld16(p00 + n * VEC);
@@ -276,6 +282,11 @@ msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float
     a.B = p.B; a.sum_hw = p.sum_hw; a.C = p.C; a.Ncam = p.Ncam; a.Nscale = p.Nscale;
     a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.scatter = scatter; a.status = dev.status;
     a.counter = counter;
+    {
+        const size_t esz = (size_t)dtype_size(p.feat_t);
+        a.wide = (p.nv == 2 && ((uintptr_t)p.feat % 32) == 0 && ((size_t)p.C * esz) % 32 == 0 &&
+                  ((size_t)p.sum_hw * p.C * esz) % 32 == 0) ? 1 : 0;
+    }
     if (counter && cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
         return check_launch("msda_backward counter");
     // persistent grid: as many blocks as fit at once, all walking one camera-major item list

@@ -37,6 +37,13 @@ __device__ __forceinline__ uint4 ld16(const void* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+// 32 bytes (p 32-byte aligned) in one 256-bit read-only load (ld.global.nc.v8.b32, sm_100 and later).
+__device__ __forceinline__ void ld32(const void* p, uint4& lo, uint4& hi) {
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+                 : "l"(p));
+}
+
 // Widen the VEC channels of one 16-byte chunk to FP32.
 __device__ __forceinline__ void widen(const uint4& v, float* f, float) {
     f[0] = __uint_as_float(v.x); f[1] = __uint_as_float(v.y);

@@ -43,6 +43,7 @@ struct FwdArgs {
     int* status;
     uint4* zero;                   // msda_forward_train: grad_feat to clear (16-byte units), or NULL
     unsigned long long zero_n16;
+    int wide;                      // a lane's two 16-byte chunks are 32-byte aligned: one 256-bit load
 };
 
 // Shared-memory carve-up of a forward block.
@@ -208,7 +209,7 @@ __device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ f
                                                         int Nscale, int P, int G, int team, int nteams,
                                                         float2* acc, const float* __restrict__ svn,
                                                         UnitRec* srec, short* slist, int* sscan,
-                                                        const ZeroSlice* zs) {
+                                                        const ZeroSlice* zs, bool wide = false) {
     constexpr int VEC = Elem<FT>::VEC;
     const int per_cam = P * Nscale;
     const int nunits = Ncam * per_cam;
@@ -279,7 +280,12 @@ __device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ f
             const FT* p00 = fb + (long long)r.row00 * C;
             const FT* p10 = p00 + (long long)r.W * C;
             uint4 q4[4][NV];
-            if ((r.wf & 15) == 15) {
+            if (NV == 2 && wide && (r.wf & 15) == 15) {
+                ld32(p00, q4[0][0], q4[0][NV - 1]);
+                ld32(p00 + C, q4[1][0], q4[1][NV - 1]);
+                ld32(p10, q4[2][0], q4[2][NV - 1]);
+                ld32(p10 + C, q4[3][0], q4[3][NV - 1]);
+            } else if ((r.wf & 15) == 15) {
 #pragma unroll
                 for (int n = 0; n < NV; ++n) {
                     q4[0][n] = ld16(p00 + n * VEC);
@@ -404,7 +410,7 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
                                                                                        kUnitsPerThread),
                                                 reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
                                                                                                  kUnitsPerThread)),
-                                                &s_zs);
+                                                &s_zs, p.wide != 0);
         else
             accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
                                           acc, p.vis ? svn : nullptr, &s_zs, lane & (p.rt - 1), p.rt);
@@ -417,7 +423,7 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
                                                                                        kUnitsPerThread),
                                                 reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
                                                                                                  kUnitsPerThread)),
-                                                nullptr);
+                                                nullptr, p.wide != 0);
         else
             accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
                                           acc, p.vis ? svn : nullptr);
@@ -607,11 +613,14 @@ __global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
             float2 acc[CPL / 2];
 #pragma unroll
             for (int j = 0; j < CPL / 2; ++j) acc[j] = make_float2(0.0f, 0.0f);
+            const bool wide = NV == 2 && ((reinterpret_cast<uintptr_t>(S.feat) & 31) == 0) &&
+                              ((size_t)p.C * sizeof(FT)) % 32 == 0;  // 256-bit loads for this scene
             accumulate_anchor_units<FT, WT, NV>(
                 fb, wb, smap, sbox, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc, nullptr,
                 reinterpret_cast<UnitRec*>(smem + lay.list),
                 reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x * kUnitsPerThread),
-                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x * kUnitsPerThread)), nullptr);
+                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x * kUnitsPerThread)), nullptr,
+                wide);
             float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
             for (int j = 0; j < CPL / 2; j += 2)
@@ -711,6 +720,10 @@ msda_status launch_forward(const Problem& p, void* out, msda_dtype out_t, int wa
     a.A = p.A; a.P = p.P; a.G = p.G; a.Cg = p.Cg; a.rt = p.rt; a.status = dev.status;
     a.zero = reinterpret_cast<uint4*>(clear);
     a.zero_n16 = clear ? clear_bytes / 16 : 0;
+    // 256-bit loads need every lane's 32 bytes aligned: the base, the row pitch and the lane pitch
+    const size_t esz = (size_t)dtype_size(p.feat_t);
+    a.wide = (p.nv == 2 && ((uintptr_t)p.feat % 32) == 0 && ((size_t)p.C * esz) % 32 == 0 &&
+              ((size_t)p.sum_hw * p.C * esz) % 32 == 0) ? 1 : 0;
     k<<<(unsigned)nblocks, warps * 32, lay.total, stream>>>(a);
     return check_launch("msda_forward");
 }
