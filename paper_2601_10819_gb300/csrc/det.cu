@@ -134,6 +134,13 @@ __device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* w
     return r;
 }
 
+// 32 FP32 bytes (p 32-byte aligned) in one 256-bit read-only load.
+__device__ __forceinline__ void ld32(const void* p, float4& lo, float4& hi) {
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+                 : "l"(p));
+}
+
 // Keys of the in-bound corners of one point-scale; bit q of the result marks corner q in bounds.
 __device__ __forceinline__ unsigned corner_keys(const KeyArgs& a, long long pt, uint32_t key[4]) {
     const int s = (int)(pt % a.Nscale);
@@ -310,6 +317,7 @@ struct RedArgs {
     const float* e_om;       // per sorted contribution: bilinear weight omega of its corner
     const uint32_t* e_pt;    //   point-scale index (t * Nscale + s)
     const uint32_t* e_ba;    //   anchor row b * A + a of grad_out
+    int wide;                // grad_out rows and lane chunks 32-byte aligned: 256-bit loads
     float* gfeat;
     long long nrows;
     int sum_hw, C, Ncam, Nscale, A, P, G, Cg, rt, sbits;
@@ -375,7 +383,15 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
             coef[u] = ldw(wp + (long long)__ldg(a.e_pt + eu) * a.G + g) * __ldg(a.e_om + eu);
             const float4* gsrc = reinterpret_cast<const float4*>(a.go + (long long)__ldg(a.e_ba + eu) * a.C + c0);
 #pragma unroll
-            for (int j = 0; j < CPL / 4; ++j) gv[u][j] = __ldg(gsrc + j);
+            for (int j = 0; j + 1 < CPL / 4; j += 2) {
+                if (a.wide) {
+                    ld32(gsrc + j, gv[u][j], gv[u][j + 1]);  // one 256-bit load for two chunks
+                } else {
+                    gv[u][j] = __ldg(gsrc + j);
+                    gv[u][j + 1] = __ldg(gsrc + j + 1);
+                }
+            }
+            if ((CPL / 4) & 1) gv[u][CPL / 4 - 1] = __ldg(gsrc + CPL / 4 - 1);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -487,6 +503,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     ra.e_om = reinterpret_cast<const float*>(kbuf[cur ^ 1]);
     ra.e_pt = vbuf[cur ^ 1];
     ra.e_ba = kbuf[cur];
+    ra.wide = (((uintptr_t)grad_out % 32) == 0 && ((size_t)p.C * 4) % 32 == 0) ? 1 : 0;
     ra.sum_hw = p.sum_hw; ra.C = p.C; ra.Ncam = p.Ncam; ra.Nscale = p.Nscale; ra.A = p.A; ra.P = p.P;
     ra.G = p.G; ra.Cg = p.Cg; ra.rt = red_rt; ra.sbits = sbits; ra.status = dev.status;
     ra.ncam = make_fastdiv((uint32_t)(p.Ncam > 0 ? p.Ncam : 1));
