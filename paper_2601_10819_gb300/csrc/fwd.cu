@@ -8,16 +8,21 @@
 // Mapping.  One block owns one anchor (b, a).  Its threads form "teams" of
 // rt lanes; a team covers the anchor's whole channel row, each lane owning
 // CPL = VEC * NV contiguous channels (VEC = 16 bytes of features), so every
-// corner read is one (NV) 16-byte load per lane and a team reads a whole
-// feature row with coalesced, sector-aligned loads.  The block's work items
-// are the (camera, keypoint) pairs in camera-major order, dealt round-robin
-// to its teams; each item covers every scale.  Because all resident blocks
-// walk the cameras in the same order, the maps being read at any moment
-// belong to a few cameras, which keeps them in L2 (the operator reads each
-// feature row about ten times).  The sampling locations of the anchor and
-// the map table are staged in shared memory first; the weights are read
-// only for points that are in view (a point whose bilinear footprint misses
-// the map costs no weight or feature traffic).
+// corner read is one 256-bit load (NV = 2, aligned) or NV 16-byte loads per
+// lane and a team reads a whole feature row with coalesced, sector-aligned
+// loads.  By default the block works in two stages per chunk of the anchor's
+// point-scales (camera, keypoint, scale) in camera-major order: the threads
+// cull and locate each point-scale once into a record in shared memory and
+// list the in-view ones in order; the teams then take the list round-robin
+// and only load and accumulate (accumulate_anchor_units).  The single-stage
+// form (accumulate_anchor, tuning variant 4) deals (camera, keypoint) items
+// to the teams and lets every lane locate the point itself.  Because all
+// resident blocks walk the cameras in the same order, the maps being read at
+// any moment belong to a few cameras, which keeps them in L2 (the operator
+// reads each feature row about ten times).  The sampling locations of the
+// anchor and the map table are staged in shared memory first; the weights
+// are read only for points that are in view (a point whose bilinear
+// footprint misses the map costs no weight or feature traffic).
 //
 // Accumulation is FP32 in registers in a fixed order; the teams' partial
 // rows are summed in team order through shared memory, so a given launch
