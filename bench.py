@@ -222,8 +222,9 @@ def l2_rates(dev, stream, tries=5):
     return gather, red
 
 
-def cpu_baseline(pr, sample_anchors):
-    """The FP64 oracle (as it stands) on the first `sample_anchors` anchors of the frame."""
+def oracle_times(pr, sample_anchors):
+    """Seconds per frame of the FP64 oracle on the first `sample_anchors` anchors, scaled to all anchors:
+    forward on all host threads and on one, backward on one."""
     import oracle
     oracle.build()
     nthreads = oracle.max_threads()
@@ -237,16 +238,35 @@ def cpu_baseline(pr, sample_anchors):
     t2 = time.perf_counter()
     oracle.forward(*args, nthreads=1)
     t3 = time.perf_counter()
+    scale = pr.sampling_location.shape[1] / sub.sampling_location.shape[1] / pr.feat.shape[0]
+    return {"fwd_all": (t1 - t0) * scale, "bwd_1": (t2 - t1) * scale, "fwd_1": (t3 - t2) * scale,
+            "raw": (t1 - t0, t2 - t1), "threads": nthreads, "anchors": sub.sampling_location.shape[1]}
+
+
+def cpu_baseline(pr, sample_anchors, others=False):
+    """The FP64 oracle (as it stands) on the first `sample_anchors` anchors of the frame; with `others`, also on
+    samples of the 6-camera and 16-camera workloads."""
+    t = oracle_times(pr, sample_anchors)
     A = pr.sampling_location.shape[1]
-    na = sub.sampling_location.shape[1]
-    per_frame_s = (t2 - t0) * A / na
-    return {"value": per_frame_s * 1e6, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"{na} of {A} anchors of one frame (fwd on {nthreads} OpenMP threads, bwd single-threaded), "
-                      f"fwd {t1 - t0:.2f} s + bwd {t2 - t1:.2f} s, scaled by {A}/{na}",
-            "fwd_us_per_frame_all_cores": (t1 - t0) * A / na * 1e6,
-            "fwd_us_per_frame_1_core": (t3 - t2) * A / na * 1e6,
-            "bwd_us_per_frame_1_core": (t2 - t1) * A / na * 1e6,
-            "host": host_info()}
+    per_frame_s = t["fwd_all"] + t["bwd_1"]
+    res = {"value": per_frame_s * 1e6, "unit": UNIT, "cores": t["threads"], "kind": "oracle",
+           "sample": f"{t['anchors']} of {A} anchors of one frame (fwd on {t['threads']} OpenMP threads, bwd "
+                     f"single-threaded), fwd {t['raw'][0]:.2f} s + bwd {t['raw'][1]:.2f} s, scaled by {A}/{t['anchors']}",
+           "fwd_us_per_frame_all_cores": t["fwd_all"] * 1e6,
+           "fwd_us_per_frame_1_core": t["fwd_1"] * 1e6,
+           "bwd_us_per_frame_1_core": t["bwd_1"] * 1e6,
+           "host": host_info()}
+    if others:
+        from paper_2601_10819_gb300 import inputs
+        res["other_workloads"] = {}
+        for name, idx, kw, n in (("sparse4d-6cam-fp32", 1, {"feat_dtype": "f32", "w_dtype": "f32"}, 300),
+                                 ("train-16cam-b4", 3, {}, 100)):
+            o = oracle_times(inputs.make_workload(idx, **kw), n)
+            res["other_workloads"][name] = {"fwd_us_per_frame_all_cores": o["fwd_all"] * 1e6,
+                                            "fwd_us_per_frame_1_core": o["fwd_1"] * 1e6,
+                                            "bwd_us_per_frame_1_core": o["bwd_1"] * 1e6,
+                                            "sample_anchors": o["anchors"]}
+    return res
 
 
 def host_info():
@@ -660,7 +680,7 @@ def main():
     if args.configs:
         line["other_workloads"] = other_configs(dev, l2_gather_gbs, l2_red_gbs, hbm_peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(pr, args.cpu_sample_anchors)
+        line["cpu_baseline"] = cpu_baseline(pr, args.cpu_sample_anchors, others=args.configs)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
