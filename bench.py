@@ -655,7 +655,15 @@ def main():
         "step_us_p50": step_us[len(step_us) // 2], "step_us_p99": step_us[min(len(step_us) - 1, int(0.99 * len(step_us)))],
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
-                     "algorithmic_bytes": dom_bytes},
+                     "algorithmic_bytes": dom_bytes,
+                     # the resource that actually binds the dominant call, measured live in this run
+                     "binding": ({"resource": "L2 FP32 vector reductions (msda_probe_reduce)",
+                                  "achieved": red_bytes / (bwd_ms * 1e-3) / 1e9, "peak": l2_red_gbs, "unit": "GB/s",
+                                  "frac": t_red_bwd / (bwd_ms * 1e3)} if dom == "msda_backward" and not det else
+                                 {"resource": "L2 random-row gathers (msda_probe_read)",
+                                  "achieved": cnt.fwd_l2_gather_bytes / (fwd_ms * 1e-3) / 1e9, "peak": l2_gather_gbs,
+                                  "unit": "GB/s", "frac": t_l2_fwd / (fwd_ms * 1e3)} if dom == "msda_forward" else
+                                 None)},
         "gather_roofline": {
             "l2_gather_gbs_measured": l2_gather_gbs,
             "l2_reduce_gbs_measured": l2_red_gbs,
