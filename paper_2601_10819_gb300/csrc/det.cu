@@ -456,7 +456,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     if (!red) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: no reduce kernel for %d channels per lane", cpl);
 
     // dloc and dw (no feature scatter)
-    st = launch_backward_loc_w(p, grad_out, grad_feat, grad_loc, grad_w, warps, 0, stream);
+    st = launch_backward_locw(p, grad_out, grad_loc, grad_w, warps, stream);
     if (st != MSDA_OK) return st;
     if (nrows == 0) return MSDA_OK;
 

@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "units.cuh"
 
 namespace msda {
 
@@ -62,8 +63,7 @@ struct FwdSmem {
         loc = vn + align16(sizeof(float) * (size_t)Ncam);
         part = loc + align16(sizeof(float2) * (size_t)P * Ncam);
         list = part + align16(sizeof(float) * (size_t)nteams * C);
-        // UnitRec entries, their 2-byte list indices, the scan scratch
-        total = list + (units ? align16(26 * (size_t)units) + 64 : 0);
+        total = list + unit_list_bytes((size_t)units);
     }
 };
 
@@ -170,42 +170,6 @@ __device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, con
 // in increasing point-scale order, so the result is deterministic; the
 // teams' shares differ from accumulate_anchor's, so the rounding does too.
 // ---------------------------------------------------------------------------
-constexpr int kUnitsPerThread = 4;
-
-struct UnitRec {
-    int row00;   // feature row of corner (y0, x0) inside the batch element (may be off the map: see the flags)
-    int W;       // map width: rows between y0 and y0 + 1
-    float fx, fy;
-    int wf;      // (index of the point-scale's weights) << 4 | vx0 | vx1 << 1 | vy0 << 2 | vy1 << 3
-    float scale; // camera factor of the fused occlusion-aware form, else 1
-};
-
-// Exclusive block-wide prefix sum (blockDim.x a multiple of 32); *total gets the sum.
-__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += t;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int w = 0; w < nw; ++w) {
-            const int t = wsum[w];
-            wsum[w] = run;
-            run += t;
-        }
-        *total = run;
-    }
-    __syncthreads();
-    const int r = x - v + wsum[warp];
-    __syncthreads();  // wsum is reused by the next call
-    return r;
-}
-
 template <typename FT, typename WT, int NV>
 __device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ fb, const WT* __restrict__ wb,
                                                         const MapInfo* __restrict__ smap,
@@ -213,8 +177,7 @@ __device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ f
                                                         const float2* __restrict__ sloc, int C, int Ncam,
                                                         int Nscale, int P, int G, int team, int nteams,
                                                         float2* acc, const float* __restrict__ svn,
-                                                        UnitRec* srec, short* slist, int* sscan,
-                                                        const ZeroSlice* zs, bool wide = false) {
+                                                        const UnitList& ul, const ZeroSlice* zs, bool wide = false) {
     constexpr int VEC = Elem<FT>::VEC;
     const int per_cam = P * Nscale;
     const int nunits = Ncam * per_cam;
@@ -237,45 +200,12 @@ __device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ f
             for (unsigned long long j = z0 + threadIdx.x; j < z1; j += blockDim.x)
                 __stcs(zs->ptr + j, make_uint4(0u, 0u, 0u, 0u));
         }
-        // stage A: cull and locate this thread's kUnitsPerThread consecutive point-scales into its own entries
-        // of the record array, then list the in-view ones, in order, by index
-        const int mine = (int)threadIdx.x * kUnitsPerThread;
-        unsigned vmask = 0u;
-#pragma unroll
-        for (int i = 0; i < kUnitsPerThread; ++i) {
-            const int u = u0 + mine + i;
-            if (u < nunits) {
-                const int k = u / per_cam;
-                const int rem = u - k * per_cam;
-                const int pp = rem / Nscale;
-                const int sc = rem - pp * Nscale;
-                const float2 uv = sloc[pp * Ncam + k];
-                const float cs = svn ? svn[k] : 1.0f;
-                const MapInfo m = smap[k * Nscale + sc];
-                Cell c;
-                if (cs != 0.0f && in_box(uv, sbox[k]) && m.W != 0 && locate(uv.x, uv.y, m.H, m.W, c)) {
-                    UnitRec r;
-                    r.row00 = m.start + c.y0 * m.W + c.x0;
-                    r.W = m.W;
-                    r.fx = c.fx;
-                    r.fy = c.fy;
-                    r.wf = ((((pp * Ncam + k) * Nscale) + sc) << 4) | (c.x0 >= 0 ? 1 : 0) |
-                           (c.x0 + 1 < m.W ? 2 : 0) | (c.y0 >= 0 ? 4 : 0) | (c.y0 + 1 < m.H ? 8 : 0);
-                    r.scale = cs;
-                    srec[mine + i] = r;
-                    vmask |= 1u << i;
-                }
-            }
-        }
-        int off = block_excl_scan(__popc(vmask), sscan, sscan + 8);
-#pragma unroll
-        for (int i = 0; i < kUnitsPerThread; ++i)
-            if (vmask & (1u << i)) slist[off++] = (short)(mine + i);
-        __syncthreads();
-        const int total = sscan[8];
+        // stage A: the chunk's in-view point-scales, located once, listed in order
+        const int total = build_unit_list(u0, nunits, P, Ncam, Nscale, smap, sbox, sloc, svn, ul,
+                                          [](int, int, int) {});
         // stage B: the teams take the list round-robin
         for (int q = team; q < total; q += nteams) {
-            const UnitRec r = srec[slist[q]];
+            const UnitRec r = ul.rec[ul.list[q]];
             const float wv = ldw(wb + (long long)(r.wf >> 4) * G) * r.scale;
             const float ax = 1.0f - r.fx, ay = 1.0f - r.fy;
             const float2 w00 = make_float2(wv * (ax * ay), wv * (ax * ay));
@@ -410,11 +340,7 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
         if constexpr (UNITS)
             accumulate_anchor_units<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team,
                                                 nteams, acc, p.vis ? svn : nullptr,
-                                                reinterpret_cast<UnitRec*>(smem + lay.list),
-                                                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x *
-                                                                                       kUnitsPerThread),
-                                                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
-                                                                                                 kUnitsPerThread)),
+                                                UnitList(smem + lay.list, (int)blockDim.x * kUnitsPerThread),
                                                 &s_zs, p.wide != 0);
         else
             accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
@@ -423,11 +349,7 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
         if constexpr (UNITS)
             accumulate_anchor_units<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team,
                                                 nteams, acc, p.vis ? svn : nullptr,
-                                                reinterpret_cast<UnitRec*>(smem + lay.list),
-                                                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x *
-                                                                                       kUnitsPerThread),
-                                                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
-                                                                                                 kUnitsPerThread)),
+                                                UnitList(smem + lay.list, (int)blockDim.x * kUnitsPerThread),
                                                 nullptr, p.wide != 0);
         else
             accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
@@ -622,10 +544,7 @@ __global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
                               ((size_t)p.C * sizeof(FT)) % 32 == 0;  // 256-bit loads for this scene
             accumulate_anchor_units<FT, WT, NV>(
                 fb, wb, smap, sbox, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc, nullptr,
-                reinterpret_cast<UnitRec*>(smem + lay.list),
-                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x * kUnitsPerThread),
-                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x * kUnitsPerThread)), nullptr,
-                wide);
+                UnitList(smem + lay.list, (int)blockDim.x * kUnitsPerThread), nullptr, wide);
             float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
             for (int j = 0; j < CPL / 2; j += 2)

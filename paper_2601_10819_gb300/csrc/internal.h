@@ -62,6 +62,9 @@ msda_status launch_backward_atomic(const Problem& p, const float* grad_out, floa
 msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float* grad_feat,
                                   float* grad_loc, float* grad_w, int warps, int scatter,
                                   cudaStream_t stream, unsigned long long* counter = nullptr);
+// dloc and dw only, one block per anchor (the deterministic modes; grad_feat is not touched).
+msda_status launch_backward_locw(const Problem& p, const float* grad_out, float* grad_loc, float* grad_w, int warps,
+                                 cudaStream_t stream);
 size_t backward_det_workspace(const Problem& p);
 msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
                                 float* grad_loc, float* grad_w, void* ws, size_t ws_bytes,

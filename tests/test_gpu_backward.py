@@ -87,7 +87,9 @@ def test_all_modes_agree():
     a = gpu_backward(pr, False)
     d = gpu_backward(pr, True)           # radix-sort rows
     st = gpu_backward(pr, True, None, 2)  # staged camera-group form
-    assert torch.equal(a[1], d[1]) and torch.equal(a[2], d[2])  # dloc, dw: same kernel, no atomics
+    # dw: the same per-scale expression and group sum in the atomic kernel and the anchor-block kernel of the
+    # radix form, no atomics (dloc sums in another fixed order: per-scale team sums, in scale order)
+    assert torch.equal(a[2], d[2])
     for x, y, z in zip(a, d, st):
         assert relerr(x.double().numpy(), y.double().numpy()) <= 1e-6
         assert relerr(x.double().numpy(), z.double().numpy()) <= 1e-6
