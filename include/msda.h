@@ -212,9 +212,10 @@ msda_status msda_keypoints(const float* anchors, const float* offsets, const flo
  *     With a workspace (256 bytes) the items are handed out from one
  *     counter strictly in camera order, which keeps the rows being
  *     accumulated in L2; with workspace = NULL a static stride is used.
- *   deterministic = 1: no atomics; bitwise reproducible.  By default the
- *     corner contributions are sorted by feature row with a global stable
- *     radix sort and each row is reduced in sorted order.  With
+ *   deterministic = 1: no floating-point atomics; bitwise reproducible.  By
+ *     default the corner contributions are grouped by feature row (a
+ *     counting sort whose integer counters place them), each row's group is
+ *     sorted by slot id, and each row is reduced in that order.  With
  *     tuning->variant = 2, when the staged kernels apply (Nscale <= 4, C/G a
  *     power of two in 4..128, at most 40960 bilinear cells per map, maps
  *     that do not overlap, A*(C/G)*4 bytes of grad_out per group fitting in

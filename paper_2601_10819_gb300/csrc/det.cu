@@ -1,16 +1,17 @@
 // MSDA backward, deterministic feature gradient (sm_103a).
 //
 // The feature gradient is a scatter: every in-bound corner of every sampled
-// point adds w_g * omega * go[c] to one feature row.  Scattering with
-// atomics makes the FP32 summation order depend on timing.  This mode
-// instead gathers: it builds, for every in-bound corner of every
-// point-scale, the key (feature row) and the value (the corner's slot id),
-// compacted in slot order, sorts the pairs by key with a stable LSD radix
-// sort, so that equal rows keep the slot order,
+// point adds w_g * omega * go[c] to one feature row.  Scattering with FP32
+// atomics makes the summation order depend on timing.  This mode instead
+// gathers: it groups the in-bound corners by feature row (a counting sort:
+// per-row counts, their prefix sum as row offsets, then every corner's slot
+// id written into its row's segment), sorts each row's segment by slot id,
 // turns the sorted slots into flat (omega, point-scale, anchor row) arrays,
-// and then lets one team per feature row sum its contributions in that
-// order and write the row once (rows nobody touches get zeros, so no memset
-// is needed).  The result is bitwise reproducible for any launch.
+// and then lets one team per feature row sum its contributions in slot order
+// and write the row once (rows nobody touches get zeros, so no memset of the
+// gradient is needed).  Integer atomics place the slot ids, in an order that
+// varies run to run, but the per-row sort fixes it, so the FP32 sums, and the
+// result, are bitwise reproducible for any launch.
 //
 // Point index t = (((b*A + a)*P + p)*Ncam + k); a corner's slot id packs
 // (t, s, q) as (t << (sbits + 2)) | (s << 2) | q, with sbits the bits of
@@ -23,41 +24,34 @@
 
 namespace msda {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kTile = kSortThreads * kSortItems;  // keys per sort block
-constexpr int kKeyPts = 4;                         // point-scales per thread in the key kernels
-constexpr int kKeyBlock = 256 * kKeyPts;           // point-scales per key block
+constexpr int kKeyPts = 4;                 // point-scales per thread in the corner kernels
+constexpr int kKeyBlock = 256 * kKeyPts;   // point-scales per corner block
+constexpr int kRowTile = 4096;             // rows per block of the row-offset scan (1024 threads x 4)
+constexpr int kSegWarps = 8;               // warps per block of the long-segment sort
+constexpr int kSegSmem = 1024;             // longest segment sorted in shared memory (per warp)
+constexpr int kLaneSeg = 16;               // longest segment a single thread sorts in registers
 
 struct DetLayout {
-    size_t n;       // slots: 4 per point-scale
+    size_t n;       // slots: 4 per point-scale (the most in-bound corners there can be)
     size_t nrows;   // B * sum_hw
-    int nb;         // sort tiles
-    int passes;     // 8-bit digit passes
-    size_t k0, v0, k1, v1, hist, tot, rowptr, cnt, nvalid, total;
-    int nkb;        // key blocks
+    int ntiles;     // row-offset scan tiles
+    size_t vals, e_om, e_pt, e_ba, cnt, rowptr, tsum, total;
 };
 
 static DetLayout det_layout(long long npts, long long nrows) {
     DetLayout L;
     L.n = (size_t)npts * 4;
     L.nrows = (size_t)nrows;
-    L.nb = (int)((L.n + kTile - 1) / kTile);
-    int bits = 0;
-    while (bits < 32 && ((unsigned long long)nrows >> bits) != 0) ++bits;  // keys go up to nrows
-    L.passes = (bits + 7) / 8;
+    L.ntiles = (int)((nrows + kRowTile - 1) / kRowTile);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    L.k0 = take(4 * L.n);
-    L.v0 = take(4 * L.n);
-    L.k1 = take(4 * L.n);
-    L.v1 = take(4 * L.n);
-    L.hist = take(4 * (size_t)256 * (L.nb > 0 ? L.nb : 1));
-    L.tot = take(4 * 256);
+    L.vals = take(4 * L.n);   // slot ids grouped by row (sorted within each row)
+    L.e_om = take(4 * L.n);   // flat arrays per contribution; e_om is also the large-segment sort's scratch
+    L.e_pt = take(4 * L.n);
+    L.e_ba = take(4 * L.n);
+    L.cnt = take(4 * (L.nrows + 1));  // per-row counts (then the list of long rows) and the list's length
     L.rowptr = take(4 * (L.nrows + 1));
-    L.nkb = (int)((npts + kKeyBlock - 1) / kKeyBlock);
-    L.cnt = take(4 * (size_t)(L.nkb > 0 ? L.nkb : 1));
-    L.nvalid = take(4);
+    L.tsum = take(4 * (size_t)(L.ntiles > 0 ? L.ntiles : 1));
     L.total = off;
     return L;
 }
@@ -68,17 +62,17 @@ size_t backward_det_workspace(const Problem& p) {
 }
 
 // ---------------------------------------------------------------------------
-// 1. Keys and slot ids
+// 1. Corners grouped by row
 // ---------------------------------------------------------------------------
 struct KeyArgs {
     const int32_t* shape;
     const int32_t* start;
     const float* loc;
-    uint32_t* keys;
-    uint32_t* vals;
     long long npts;
     int sum_hw, A, P, Ncam, Nscale, sbits;
-    uint32_t* counts;  // per key block: in-bound corners (count pass), then their exclusive prefix (write pass)
+    uint32_t* cnt;           // per row: in-bound corners (count pass); counted down by the fill pass
+    const uint32_t* rowptr;  // row offsets (fill pass)
+    uint32_t* vals;          // slot ids grouped by row (fill pass)
     int* status;
 };
 
@@ -163,143 +157,195 @@ __device__ __forceinline__ unsigned corner_keys(const KeyArgs& a, long long pt, 
 }
 
 // Block b handles point-scales [b*kKeyBlock, (b+1)*kKeyBlock), kKeyPts consecutive ones per thread.  The count
-// pass stores the block's number of in-bound corners; the write pass stores only those corners' (key, slot)
-// pairs, at the block's prefix plus the thread's prefix inside the block, so the pairs stay in slot order
-// (which the stable sort keeps for equal keys) and the sort sees no out-of-bounds corners at all.
-template <bool WRITE>
-__global__ void __launch_bounds__(256) det_keys_kernel(const KeyArgs a) {
-    __shared__ uint32_t ws[32];
+// pass adds each in-bound corner to its row's count; the fill pass takes a place in the row's segment for it
+// (counting the row down) and stores the corner's slot id there.  Both passes see the same corners, so a row
+// never runs out of places; the check only keeps a store inside the row if they ever differed.
+template <bool FILL>
+__global__ void __launch_bounds__(256) det_rows_kernel(const KeyArgs a) {
     const long long base = (long long)blockIdx.x * kKeyBlock + (long long)threadIdx.x * kKeyPts;
-    uint32_t key[kKeyPts][4];
-    unsigned mask[kKeyPts];
-    uint32_t cnt = 0u;
-#pragma unroll
-    for (int i = 0; i < kKeyPts; ++i) {
-        mask[i] = (base + i < a.npts) ? corner_keys(a, base + i, key[i]) : 0u;
-        cnt += (uint32_t)__popc(mask[i]);
-    }
-    uint32_t total;
-    const uint32_t incl = block_inclusive_scan<8>(cnt, ws, &total);
-    if (!WRITE) {
-        if (threadIdx.x == 0) a.counts[blockIdx.x] = total;
-        return;
-    }
-    uint32_t off = a.counts[blockIdx.x] + incl - cnt;
 #pragma unroll
     for (int i = 0; i < kKeyPts; ++i) {
         const long long pt = base + i;
+        if (pt >= a.npts) break;
+        uint32_t key[4];
+        const unsigned mask = corner_keys(a, pt, key);
         const uint32_t slot = ((((uint32_t)(pt / a.Nscale)) << a.sbits) | (uint32_t)(pt % a.Nscale)) << 2;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (mask[i] & (1u << q)) {
-                a.keys[off] = key[i][q];
-                a.vals[off] = slot + (uint32_t)q;
-                ++off;
+            if (!(mask & (1u << q))) continue;
+            if (!FILL) {
+                atomicAdd(a.cnt + key[q], 1u);
+            } else {
+                const uint32_t r0 = a.rowptr[key[q]], len = a.rowptr[key[q] + 1] - r0;
+                const uint32_t left = atomicSub(a.cnt + key[q], 1u);  // places left in the row, this one included
+                if (left - 1u < len)
+                    a.vals[r0 + left - 1u] = slot + (uint32_t)q;
+                else
+                    raise_status(a.status, MSDA_ERR_OUT_OF_RANGE);
             }
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// 2. Stable LSD radix sort, 8-bit digits: histogram, per-digit scan, scatter
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t* __restrict__ keys,
-                                                                  const uint32_t* __restrict__ n_dev, int shift,
-                                                                  uint32_t* __restrict__ hist, int nb) {
-    const size_t n = *n_dev;  // keys to sort (the grid covers the most there can be)
-    const size_t base = (size_t)blockIdx.x * kTile;
-    if (base >= n) {  // a tile past the keys: empty counts (uniform over the block)
-        hist[(size_t)threadIdx.x * nb + blockIdx.x] = 0u;
-        return;
+// Row offsets, step 1: per tile of kRowTile rows, the exclusive prefix of the counts inside the tile, and the
+// tile's total.
+__global__ void __launch_bounds__(1024) row_scan_tile_kernel(const uint32_t* __restrict__ cnt, long long nrows,
+                                                             uint32_t* __restrict__ rowptr,
+                                                             uint32_t* __restrict__ tsum) {
+    __shared__ uint32_t ws[32];
+    const long long r0 = (long long)blockIdx.x * kRowTile + (long long)threadIdx.x * 4;
+    uint32_t v[4], s = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[j] = (r0 + j < nrows) ? cnt[r0 + j] : 0u;
+        s += v[j];
     }
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-#pragma unroll 4
-    for (int r = 0; r < kSortItems; ++r) {
-        const size_t i = base + (size_t)r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(__ldg(keys + i) >> shift) & 255u], 1u);
+    uint32_t tot;
+    uint32_t run = block_inclusive_scan<32>(s, ws, &tot) - s;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (r0 + j < nrows) rowptr[r0 + j] = run;
+        run += v[j];
     }
-    __syncthreads();
-    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+    if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
 }
 
-// Block d turns hist[d][0..nb) into exclusive prefixes and writes totals[d].
-__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ hist, int nb,
-                                                          uint32_t* __restrict__ totals) {
+// Step 2 (one block): the tile totals become their exclusive prefix; *total gets the number of corners.
+__global__ void __launch_bounds__(1024) row_scan_totals_kernel(uint32_t* __restrict__ tsum, int ntiles,
+                                                               uint32_t* __restrict__ total) {
     __shared__ uint32_t ws[32];
-    uint32_t* h = hist + (size_t)blockIdx.x * nb;
-    uint32_t carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
+    uint32_t carry = 0u;
+    for (int base = 0; base < ntiles; base += 1024) {
         const int i = base + threadIdx.x;
-        const uint32_t v = i < nb ? h[i] : 0u;
+        const uint32_t v = i < ntiles ? tsum[i] : 0u;
         uint32_t tot;
         const uint32_t incl = block_inclusive_scan<32>(v, ws, &tot);
-        if (i < nb) h[i] = carry + incl - v;
+        if (i < ntiles) tsum[i] = carry + incl - v;
         carry += tot;
     }
-    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+    if (threadIdx.x == 0) *total = carry;
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
-    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ hist,
-    const uint32_t* __restrict__ totals, int nb) {
-    const size_t n = *n_dev;
-    if ((size_t)blockIdx.x * kTile >= n) return;  // a tile past the keys (uniform over the block)
-    constexpr int NW = kSortThreads / 32;
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wcnt[NW][256];
-    __shared__ uint32_t ws[32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    {
-        const uint32_t tot = totals[t];
-        const uint32_t incl = block_inclusive_scan<NW>(tot, ws, nullptr);
-        base[t] = incl - tot + hist[(size_t)t * nb + blockIdx.x];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) wcnt[w][t] = 0u;
-    }
-    __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    const size_t tile = (size_t)blockIdx.x * kTile;
-    for (int r = 0; r < kSortItems; ++r) {
-        const size_t i = tile + (size_t)r * kSortThreads + t;
-        const bool ok = i < n;
-        const uint32_t key = ok ? kin[i] : 0u;
-        const uint32_t val = ok ? vin[i] : 0u;
-        const int d = ok ? (int)((key >> shift) & 255u) : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & lt);
-        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] = (uint32_t)__popc(peers);
-        __syncthreads();
-        if (ok) {
-            uint32_t pos = base[d] + rank;
-            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-            kout[pos] = key;
-            vout[pos] = val;
+// Step 3: each row offset gets its tile's prefix.
+__global__ void __launch_bounds__(256) row_scan_add_kernel(uint32_t* __restrict__ rowptr,
+                                                           const uint32_t* __restrict__ tsum, long long nrows) {
+    for (long long r = (long long)blockIdx.x * 256 + threadIdx.x; r < nrows; r += (long long)gridDim.x * 256)
+        rowptr[r] += tsum[r / kRowTile];
+}
+
+// Segment sort, pass 1 of 2 (every row's slot ids ascending): one thread per row sorts a segment of up to
+// kLaneSeg slots in registers (odd-even transposition); the longer rows are appended to a list (in any
+// order: each row is sorted on its own) for pass 2.
+__global__ void __launch_bounds__(256) det_segsort_short_kernel(const uint32_t* __restrict__ rowptr,
+                                                                long long nrows, uint32_t* __restrict__ vals,
+                                                                uint32_t* __restrict__ longrows,
+                                                                uint32_t* __restrict__ nlong) {
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long end = (nrows + 31) & ~31ll;  // whole warps iterate together
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < end; r += stride) {
+        uint32_t e0 = 0u, n = 0u;
+        if (r < nrows) {
+            e0 = rowptr[r];
+            n = rowptr[r + 1] - e0;
         }
-        __syncthreads();
-        uint32_t sum = 0;
+        if (n > 1u && n <= (uint32_t)kLaneSeg) {
+            uint32_t v[kLaneSeg];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            sum += wcnt[w][t];
-            wcnt[w][t] = 0u;
+            for (int j = 0; j < kLaneSeg; ++j) v[j] = ((uint32_t)j < n) ? vals[e0 + j] : 0xffffffffu;
+#pragma unroll
+            for (int rd = 0; rd < kLaneSeg; ++rd) {
+#pragma unroll
+                for (int j = rd & 1; j + 1 < kLaneSeg; j += 2) {
+                    const uint32_t lo = min(v[j], v[j + 1]), hi = max(v[j], v[j + 1]);
+                    v[j] = lo;
+                    v[j + 1] = hi;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kLaneSeg; ++j)
+                if ((uint32_t)j < n) vals[e0 + j] = v[j];
         }
-        base[t] += sum;
-        __syncthreads();
+        const bool lng = n > (uint32_t)kLaneSeg;
+        const unsigned bal = __ballot_sync(0xffffffffu, lng);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            uint32_t at = 0u;
+            if (lane == leader) at = atomicAdd(nlong, (uint32_t)__popc(bal));
+            at = __shfl_sync(0xffffffffu, at, leader);
+            if (lng) longrows[at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)r;
+        }
     }
 }
 
-// rowptr[r] = number of sorted keys < r, for r in [0, nrows].
-__global__ void __launch_bounds__(256) row_ptr_kernel(const uint32_t* __restrict__ ks,
-                                                      const uint32_t* __restrict__ n_dev, uint32_t nrows,
-                                                      uint32_t* __restrict__ rowptr) {
-    const size_t n = *n_dev;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i <= n; i += (size_t)gridDim.x * blockDim.x) {
-        const unsigned long long lo = (i == 0) ? 0ull : (unsigned long long)ks[i - 1] + 1ull;
-        unsigned long long hi = (i == n) ? (unsigned long long)nrows : (unsigned long long)ks[i];
-        if (hi > nrows) hi = nrows;
-        for (unsigned long long r = lo; r <= hi; ++r) rowptr[r] = (uint32_t)i;
+// Ascending bitonic sort of one value per lane across the warp.
+__device__ __forceinline__ uint32_t warp_sort32(uint32_t x, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+            const bool up = (lane & k) == 0, low = (lane & j) == 0;
+            x = (up == low) ? min(x, y) : max(x, y);
+        }
+    }
+    return x;
+}
+
+// Segment sort, pass 2: one warp per listed row: up to 32 slots with shuffles, up to kSegSmem with a bitonic sort in shared
+// memory, longer ones by rank (every slot counts the smaller ones; slot ids are distinct) through the scratch
+// array.
+__global__ void __launch_bounds__(kSegWarps * 32) det_segsort_long_kernel(const uint32_t* __restrict__ rowptr,
+                                                                          const uint32_t* __restrict__ longrows,
+                                                                          const uint32_t* __restrict__ nlong,
+                                                                          uint32_t* __restrict__ vals,
+                                                                          uint32_t* __restrict__ scratch) {
+    __shared__ uint32_t sbuf[kSegWarps][kSegSmem];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* buf = sbuf[warp];
+    const uint32_t nl = *nlong;
+    for (uint32_t li = blockIdx.x * kSegWarps + warp; li < nl; li += gridDim.x * kSegWarps) {
+        const uint32_t r = longrows[li];
+        const uint32_t b0 = rowptr[r], m = rowptr[r + 1] - b0;
+        uint32_t* v = vals + b0;
+        if (m <= 32u) {
+            uint32_t x = ((uint32_t)lane < m) ? v[lane] : 0xffffffffu;
+            x = warp_sort32(x, lane);
+            if ((uint32_t)lane < m) v[lane] = x;
+        } else if (m <= (uint32_t)kSegSmem) {
+            uint32_t p2 = 64u;
+            while (p2 < m) p2 <<= 1;
+            for (uint32_t i = lane; i < p2; i += 32) buf[i] = (i < m) ? v[i] : 0xffffffffu;
+            __syncwarp();
+            for (uint32_t k = 2; k <= p2; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t i = lane; i < p2; i += 32) {
+                        const uint32_t ij = i ^ j;
+                        if (ij > i) {
+                            const uint32_t x = buf[i], y = buf[ij];
+                            if ((x > y) == ((i & k) == 0)) {
+                                buf[i] = y;
+                                buf[ij] = x;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (uint32_t i = lane; i < m; i += 32) v[i] = buf[i];
+            __syncwarp();  // buf is reused by the next row
+        } else {
+            uint32_t* w = scratch + b0;
+            for (uint32_t i = lane; i < m; i += 32) {
+                const uint32_t x = v[i];
+                uint32_t rank = 0u;
+                for (uint32_t j = 0; j < m; ++j) rank += (v[j] < x) ? 1u : 0u;
+                w[rank] = x;
+            }
+            __syncwarp();
+            for (uint32_t i = lane; i < m; i += 32) v[i] = w[i];
+            __syncwarp();
+        }
     }
 }
 
@@ -461,48 +507,46 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     if (nrows == 0) return MSDA_OK;
 
     unsigned char* base = reinterpret_cast<unsigned char*>(ws);
-    uint32_t* kbuf[2] = {reinterpret_cast<uint32_t*>(base + L.k0), reinterpret_cast<uint32_t*>(base + L.k1)};
-    uint32_t* vbuf[2] = {reinterpret_cast<uint32_t*>(base + L.v0), reinterpret_cast<uint32_t*>(base + L.v1)};
-    uint32_t* hist = reinterpret_cast<uint32_t*>(base + L.hist);
-    uint32_t* tot = reinterpret_cast<uint32_t*>(base + L.tot);
+    uint32_t* vals = reinterpret_cast<uint32_t*>(base + L.vals);
+    uint32_t* e_om = reinterpret_cast<uint32_t*>(base + L.e_om);
+    uint32_t* e_pt = reinterpret_cast<uint32_t*>(base + L.e_pt);
+    uint32_t* e_ba = reinterpret_cast<uint32_t*>(base + L.e_ba);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(base + L.cnt);
     uint32_t* rowptr = reinterpret_cast<uint32_t*>(base + L.rowptr);
-    int cur = 0;
-    uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.cnt);
-    uint32_t* nvalid = reinterpret_cast<uint32_t*>(base + L.nvalid);
-    if (cudaMemsetAsync(nvalid, 0, sizeof(uint32_t), stream) != cudaSuccess) return check_launch("msda_backward");
-    if (npts > 0) {
-        KeyArgs ka;
-        ka.shape = p.shape; ka.start = p.start; ka.loc = p.loc; ka.keys = kbuf[0]; ka.vals = vbuf[0];
-        ka.npts = npts; ka.sum_hw = p.sum_hw; ka.A = p.A; ka.P = p.P; ka.Ncam = p.Ncam;
-        ka.Nscale = p.Nscale; ka.sbits = sbits; ka.counts = counts; ka.status = dev.status;
-        // in-bound corners per key block, their prefix (and total), then the compacted (key, slot) pairs
-        det_keys_kernel<false><<<L.nkb, 256, 0, stream>>>(ka);
-        radix_scan_kernel<<<1, 1024, 0, stream>>>(counts, L.nkb, nvalid);
-        det_keys_kernel<true><<<L.nkb, 256, 0, stream>>>(ka);
-        if ((st = check_launch("msda_backward keys")) != MSDA_OK) return st;
-        for (int pass = 0; pass < L.passes; ++pass) {
-            const int shift = 8 * pass;
-            radix_hist_kernel<<<L.nb, kSortThreads, 0, stream>>>(kbuf[cur], nvalid, shift, hist, L.nb);
-            radix_scan_kernel<<<256, 1024, 0, stream>>>(hist, L.nb, tot);
-            radix_scatter_kernel<<<L.nb, kSortThreads, 0, stream>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1],
-                                                                    vbuf[cur ^ 1], nvalid, shift, hist, tot, L.nb);
-            if ((st = check_launch("msda_backward sort")) != MSDA_OK) return st;
-            cur ^= 1;
-        }
-    }
+    uint32_t* tsum = reinterpret_cast<uint32_t*>(base + L.tsum);
+    KeyArgs ka;
+    ka.shape = p.shape; ka.start = p.start; ka.loc = p.loc; ka.npts = npts; ka.sum_hw = p.sum_hw; ka.A = p.A;
+    ka.P = p.P; ka.Ncam = p.Ncam; ka.Nscale = p.Nscale; ka.sbits = sbits; ka.cnt = cnt; ka.rowptr = rowptr;
+    ka.vals = vals; ka.status = dev.status;
+    const long long nkb = (npts + kKeyBlock - 1) / kKeyBlock;
+    // per-row counts of the in-bound corners, row offsets (three-step scan), then the slot ids in place
+    if (cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(nrows + 1), stream) != cudaSuccess)
+        return check_launch("msda_backward memset");
+    if (nkb > 0) det_rows_kernel<false><<<(unsigned)nkb, 256, 0, stream>>>(ka);
+    row_scan_tile_kernel<<<(unsigned)L.ntiles, 1024, 0, stream>>>(cnt, nrows, rowptr, tsum);
+    row_scan_totals_kernel<<<1, 1024, 0, stream>>>(tsum, L.ntiles, rowptr + nrows);
     {
-        long long rb = ((long long)L.n + 1 + 255) / 256;
-        if (rb > (long long)dev.sm_count * 32) rb = (long long)dev.sm_count * 32;
-        row_ptr_kernel<<<(unsigned)rb, 256, 0, stream>>>(kbuf[cur], nvalid, (uint32_t)nrows, rowptr);
-        if ((st = check_launch("msda_backward row offsets")) != MSDA_OK) return st;
+        long long ab = (nrows + 255) / 256;
+        if (ab > (long long)dev.sm_count * 16) ab = (long long)dev.sm_count * 16;
+        row_scan_add_kernel<<<(unsigned)ab, 256, 0, stream>>>(rowptr, tsum, nrows);
+    }
+    if ((st = check_launch("msda_backward row offsets")) != MSDA_OK) return st;
+    if (nkb > 0) {
+        det_rows_kernel<true><<<(unsigned)nkb, 256, 0, stream>>>(ka);
+        // the per-row counts are all zero again after the fill: their array takes the list of long rows
+        long long sb = (nrows + 255) / 256;
+        if (sb > (long long)dev.sm_count * 16) sb = (long long)dev.sm_count * 16;
+        det_segsort_short_kernel<<<(unsigned)sb, 256, 0, stream>>>(rowptr, nrows, vals, cnt, cnt + nrows);
+        det_segsort_long_kernel<<<(unsigned)dev.sm_count * 8, kSegWarps * 32, 0, stream>>>(rowptr, cnt, cnt + nrows,
+                                                                                          vals, e_om);
+        if ((st = check_launch("msda_backward row groups")) != MSDA_OK) return st;
     }
     RedArgs ra;
     ra.shape = p.shape; ra.start = p.start; ra.loc = p.loc; ra.w = p.w; ra.go = grad_out;
-    ra.vals = vbuf[cur]; ra.rowptr = rowptr; ra.gfeat = grad_feat; ra.nrows = nrows;
-    // the sorted keys and the other sort buffers are free once the row offsets exist
-    ra.e_om = reinterpret_cast<const float*>(kbuf[cur ^ 1]);
-    ra.e_pt = vbuf[cur ^ 1];
-    ra.e_ba = kbuf[cur];
+    ra.vals = vals; ra.rowptr = rowptr; ra.gfeat = grad_feat; ra.nrows = nrows;
+    ra.e_om = reinterpret_cast<const float*>(e_om);
+    ra.e_pt = e_pt;
+    ra.e_ba = e_ba;
     ra.wide = (((uintptr_t)grad_out % 32) == 0 && ((size_t)p.C * 4) % 32 == 0) ? 1 : 0;
     ra.sum_hw = p.sum_hw; ra.C = p.C; ra.Ncam = p.Ncam; ra.Nscale = p.Nscale; ra.A = p.A; ra.P = p.P;
     ra.G = p.G; ra.Cg = p.Cg; ra.rt = red_rt; ra.sbits = sbits; ra.status = dev.status;
@@ -513,8 +557,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
         if ((st = ensure_smem((const void*)det_prep_kernel, smem, dev)) != MSDA_OK) return st;
         long long pb = ((long long)L.n + 255) / 256;
         if (pb > (long long)dev.sm_count * 32) pb = (long long)dev.sm_count * 32;
-        det_prep_kernel<<<(unsigned)pb, 256, smem, stream>>>(ra, L.n, reinterpret_cast<float*>(kbuf[cur ^ 1]),
-                                                             vbuf[cur ^ 1], kbuf[cur]);
+        det_prep_kernel<<<(unsigned)pb, 256, smem, stream>>>(ra, L.n, reinterpret_cast<float*>(e_om), e_pt, e_ba);
         if ((st = check_launch("msda_backward prep")) != MSDA_OK) return st;
     }
     const int nteams = 8 * (32 / red_rt);

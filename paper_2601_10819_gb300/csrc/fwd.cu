@@ -177,7 +177,8 @@ __device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ f
                                                         const float2* __restrict__ sloc, int C, int Ncam,
                                                         int Nscale, int P, int G, int team, int nteams,
                                                         float2* acc, const float* __restrict__ svn,
-                                                        const UnitList& ul, const ZeroSlice* zs, bool wide = false) {
+                                                        UnitRec* srec, short* slist, int* sscan,
+                                                        const ZeroSlice* zs, bool wide = false) {
     constexpr int VEC = Elem<FT>::VEC;
     const int per_cam = P * Nscale;
     const int nunits = Ncam * per_cam;
@@ -200,12 +201,45 @@ __device__ __forceinline__ void accumulate_anchor_units(const FT* __restrict__ f
             for (unsigned long long j = z0 + threadIdx.x; j < z1; j += blockDim.x)
                 __stcs(zs->ptr + j, make_uint4(0u, 0u, 0u, 0u));
         }
-        // stage A: the chunk's in-view point-scales, located once, listed in order
-        const int total = build_unit_list(u0, nunits, P, Ncam, Nscale, smap, sbox, sloc, svn, ul,
-                                          [](int, int, int) {});
+        // stage A: cull and locate this thread's kUnitsPerThread consecutive point-scales into its own entries
+        // of the record array, then list the in-view ones, in order, by index
+        const int mine = (int)threadIdx.x * kUnitsPerThread;
+        unsigned vmask = 0u;
+#pragma unroll
+        for (int i = 0; i < kUnitsPerThread; ++i) {
+            const int u = u0 + mine + i;
+            if (u < nunits) {
+                const int k = u / per_cam;
+                const int rem = u - k * per_cam;
+                const int pp = rem / Nscale;
+                const int sc = rem - pp * Nscale;
+                const float2 uv = sloc[pp * Ncam + k];
+                const float cs = svn ? svn[k] : 1.0f;
+                const MapInfo m = smap[k * Nscale + sc];
+                Cell c;
+                if (cs != 0.0f && in_box(uv, sbox[k]) && m.W != 0 && locate(uv.x, uv.y, m.H, m.W, c)) {
+                    UnitRec r;
+                    r.row00 = m.start + c.y0 * m.W + c.x0;
+                    r.W = m.W;
+                    r.fx = c.fx;
+                    r.fy = c.fy;
+                    r.wf = ((((pp * Ncam + k) * Nscale) + sc) << 4) | (c.x0 >= 0 ? 1 : 0) |
+                           (c.x0 + 1 < m.W ? 2 : 0) | (c.y0 >= 0 ? 4 : 0) | (c.y0 + 1 < m.H ? 8 : 0);
+                    r.scale = cs;
+                    srec[mine + i] = r;
+                    vmask |= 1u << i;
+                }
+            }
+        }
+        int off = block_excl_scan(__popc(vmask), sscan, sscan + 8);
+#pragma unroll
+        for (int i = 0; i < kUnitsPerThread; ++i)
+            if (vmask & (1u << i)) slist[off++] = (short)(mine + i);
+        __syncthreads();
+        const int total = sscan[8];
         // stage B: the teams take the list round-robin
         for (int q = team; q < total; q += nteams) {
-            const UnitRec r = ul.rec[ul.list[q]];
+            const UnitRec r = srec[slist[q]];
             const float wv = ldw(wb + (long long)(r.wf >> 4) * G) * r.scale;
             const float ax = 1.0f - r.fx, ay = 1.0f - r.fy;
             const float2 w00 = make_float2(wv * (ax * ay), wv * (ax * ay));
@@ -340,7 +374,11 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
         if constexpr (UNITS)
             accumulate_anchor_units<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team,
                                                 nteams, acc, p.vis ? svn : nullptr,
-                                                UnitList(smem + lay.list, (int)blockDim.x * kUnitsPerThread),
+                                                reinterpret_cast<UnitRec*>(smem + lay.list),
+                                                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x *
+                                                                                       kUnitsPerThread),
+                                                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
+                                                                                                 kUnitsPerThread)),
                                                 &s_zs, p.wide != 0);
         else
             accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
@@ -349,7 +387,11 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 1)) fwd_anch
         if constexpr (UNITS)
             accumulate_anchor_units<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team,
                                                 nteams, acc, p.vis ? svn : nullptr,
-                                                UnitList(smem + lay.list, (int)blockDim.x * kUnitsPerThread),
+                                                reinterpret_cast<UnitRec*>(smem + lay.list),
+                                                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x *
+                                                                                       kUnitsPerThread),
+                                                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x *
+                                                                                                 kUnitsPerThread)),
                                                 nullptr, p.wide != 0);
         else
             accumulate_anchor<FT, WT, NV>(fb, wb, smap, sbox, sloc, p.C, p.Ncam, p.Nscale, p.P, p.G, team, nteams,
@@ -544,7 +586,10 @@ __global__ void __launch_bounds__(256) fwd_batched_kernel(const BatchedArgs p) {
                               ((size_t)p.C * sizeof(FT)) % 32 == 0;  // 256-bit loads for this scene
             accumulate_anchor_units<FT, WT, NV>(
                 fb, wb, smap, sbox, sloc, p.C, ncam, p.Nscale, p.P, p.G, team, nteams, acc, nullptr,
-                UnitList(smem + lay.list, (int)blockDim.x * kUnitsPerThread), nullptr, wide);
+                reinterpret_cast<UnitRec*>(smem + lay.list),
+                reinterpret_cast<short*>(smem + lay.list + 24 * (size_t)blockDim.x * kUnitsPerThread),
+                reinterpret_cast<int*>(smem + lay.list + align16(26 * (size_t)blockDim.x * kUnitsPerThread)), nullptr,
+                wide);
             float* mine = spart + (size_t)team * p.C + c0;
 #pragma unroll
             for (int j = 0; j < CPL / 2; j += 2)

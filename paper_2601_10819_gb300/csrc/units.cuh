@@ -8,7 +8,10 @@
 // lists the in-view ones in increasing u with a block scan.  Stage B (in the
 // kernels) deals the list round-robin to the block's teams, which only load
 // the corner rows and do their arithmetic; a team meets its records in
-// increasing u, so its sums run in a fixed order.
+// increasing u, so its sums run in a fixed order.  The forward kernels
+// (fwd.cu) write the same stage A out inline, between their zero stores:
+// built through build_unit_list, the training forward ran 24 us slower on the
+// 64-camera workload.
 #pragma once
 
 #include "common.cuh"

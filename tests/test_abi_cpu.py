@@ -101,7 +101,7 @@ def test_workspace_sizes(lib):
     assert lib.msda_backward_workspace_size(1, 100, 32, 2, 2, 4, 3, 4, 0) == 256  # atomic mode: work counter
     n = 1 * 4 * 3 * 2 * 2
     ws = lib.msda_backward_workspace_size(1, 100, 32, 2, 2, 4, 3, 4, 1)
-    assert ws >= 4 * 4 * n * 4 + 4 * 101  # keys, values (double-buffered) and row offsets
+    assert ws >= 4 * 4 * n * 4 + 4 * 101  # slot ids, three flat arrays per contribution, row offsets
     assert lib.msda_forward_batched_workspace_size(16) >= 17 * 4
 
 

@@ -34,7 +34,7 @@ def check_against_oracle(pr, grads, tol, label=""):
     return errs
 
 
-# (deterministic, variant): atomic scatter, radix-sort deterministic, staged deterministic
+# (deterministic, variant): atomic scatter, row-grouped deterministic, staged deterministic
 MODES = [(False, 0), (True, 0), (True, 2)]
 
 
@@ -85,10 +85,10 @@ def test_deterministic_mode_is_bitwise_reproducible(variant):
 def test_all_modes_agree():
     pr = inputs.make_workload(2, ncam=8)
     a = gpu_backward(pr, False)
-    d = gpu_backward(pr, True)           # radix-sort rows
+    d = gpu_backward(pr, True)           # rows grouped by a counting sort
     st = gpu_backward(pr, True, None, 2)  # staged camera-group form
     # dw: the same per-scale expression and group sum in the atomic kernel and the anchor-block kernel of the
-    # radix form, no atomics (dloc sums in another fixed order: per-scale team sums, in scale order)
+    # row-grouped form, no atomics (dloc sums in another fixed order: per-scale team sums, in scale order)
     assert torch.equal(a[2], d[2])
     for x, y, z in zip(a, d, st):
         assert relerr(x.double().numpy(), y.double().numpy()) <= 1e-6
@@ -184,8 +184,8 @@ def test_uncovered_rows_are_zero_and_overlaps_reported():
     ov = inputs.Problem(pr.feat, pr.spatial_shape, start, pr.sampling_location, pr.weights, pr.grad_out)
     gpu_backward(ov, True, None, 2)  # the staged form needs disjoint maps and reports the overlap
     assert msda.device_status() == 5
-    g = gpu_backward(ov, True)  # the radix form handles overlapping maps
-    check_against_oracle(ov, g, TOL_FP32, "overlapping maps, radix form")
+    g = gpu_backward(ov, True)  # the row-grouped form handles overlapping maps
+    check_against_oracle(ov, g, TOL_FP32, "overlapping maps, row-grouped form")
     assert msda.device_status() == 0
 
 
@@ -367,3 +367,35 @@ def test_bench_step_in_its_launch_configuration_full_size():
         print(f"bench step {name} rel err {e:.2e}")
         assert e <= TOL_LOWP_GRAD
     assert msda.device_status() == 0
+
+
+@pytest.mark.parametrize("G", [4, 2])
+def test_deterministic_large_anchor_takes_the_per_point_kernel(G):
+    """An anchor whose point-scales do not fit the anchor-block kernel's shared memory (100 keypoints x 64 cameras
+    x 4 scales) takes the per-point kernel for dloc and dw; the result still matches the oracle and is bitwise
+    reproducible.  G = 2 exercises the scalar zero stores of dropped point-scales in the anchor-block kernel's
+    small case below, G = 4 the 16-byte ones."""
+    gen = torch.Generator().manual_seed(64 + G)
+    maps = [[(6, 5), (3, 3), (2, 2), (1, 1)]] * 64
+    pr = inputs.make_problem(gen, B=1, cam_maps=maps, C=32, G=G, A=3, P=100, loc_range=(-0.5, 1.5))
+    a = gpu_backward(pr, True, 8)
+    b = gpu_backward(pr, True, 4)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    check_against_oracle(pr, a, TOL_FP32, f"large anchor G={G}")
+    small = inputs.make_problem(gen, B=1, cam_maps=maps, C=32, G=G, A=3, P=3, loc_range=(-0.5, 1.5))
+    check_against_oracle(small, gpu_backward(small, True, 4), TOL_FP32, f"64 cameras, small anchor G={G}")
+
+
+def test_deterministic_rows_with_thousands_of_contributions():
+    """Every point falls on the same few feature rows (2x2 and 1x1 maps), so each row gathers about 1600
+    contributions: the per-row sort takes its rank path (more than 1024 slots), and a medium case (about 40 per
+    row) its shared-memory path; both match the oracle and are bitwise reproducible over launches."""
+    gen = torch.Generator().manual_seed(1600)
+    for maps, A in (([[(2, 2), (1, 1)]] * 2, 200), ([[(4, 4), (2, 3)]] * 3, 12)):
+        pr = inputs.make_problem(gen, B=1, cam_maps=maps, C=32, G=4, A=A, P=8, loc_range=(0.0, 1.0))
+        a = gpu_backward(pr, True, 8)
+        b = gpu_backward(pr, True, 2)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+        check_against_oracle(pr, a, TOL_FP32, f"many contributions per row A={A}")
