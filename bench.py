@@ -614,6 +614,30 @@ def main():
     torch.cuda.synchronize(dev)
     e2e_ms = max_over_ranks([s0.elapsed_time(s1) / args.e2e_steps], dev)[0]
 
+    # the same copies alone (one step's inputs in and outputs out, both directions at once): the floor of the
+    # end-to-end step on this host link
+    def copies_only():
+        s_in[0].wait_stream(main)
+        s_out[0].wait_stream(main)
+        with torch.cuda.stream(s_in[0]):
+            for dd, ss in zip(slots[0][0], h_in):
+                dd.copy_(ss, non_blocking=True)
+        with torch.cuda.stream(s_out[0]):
+            for dd, ss in zip(slots[1][2], slots[1][1]):
+                dd.copy_(ss, non_blocking=True)
+        main.wait_stream(s_in[0])
+        main.wait_stream(s_out[0])
+
+    copies_only()
+    torch.cuda.synchronize(dev)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(main)
+    for _ in range(3):
+        copies_only()
+    c1.record(main)
+    torch.cuda.synchronize(dev)
+    copy_ms = max_over_ranks([c0.elapsed_time(c1) / 3], dev)[0]
+
     hbm_peak, peak_src = peaks()
     feat_mb = d.feat.numel() * d.feat.element_size() / 1e6
     gf_mb = gf.numel() * 4 / 1e6
@@ -675,8 +699,10 @@ def main():
         "e2e": {"value": e2e_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps,
                 "pipeline": f"copy-in, compute and copy-out of consecutive steps overlap (2 buffer sets; each "
-                            f"direction's copies cut over {nsplit} streams)"},
-        "gpu_launches": ((2 if fwd_ws is not None and not fwd_clear else 1) + (1 if not det else 9)) * args.steps,
+                            f"direction's copies cut over {nsplit} streams)",
+                "copy_floor": {"value": copy_ms * 1e3 / B, "unit": UNIT, "frac": copy_ms / e2e_ms,
+                               "what": "the step's host<->device copies alone, both directions at once"}},
+        "gpu_launches": ((2 if fwd_ws is not None and not fwd_clear else 1) + (1 if not det else 10)) * args.steps,
         "tuning": {"forward": ft, "backward": bt},
         "clocks": clk.summary(),
         "gpu": torch.cuda.get_device_name(dev),
