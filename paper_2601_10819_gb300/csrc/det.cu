@@ -292,9 +292,57 @@ __device__ __forceinline__ uint32_t warp_sort32(uint32_t x, int lane) {
     return x;
 }
 
-// Segment sort, pass 2: one warp per listed row: up to 32 slots with shuffles, up to kSegSmem with a bitonic sort in shared
-// memory, longer ones by rank (every slot counts the smaller ones; slot ids are distinct) through the scratch
-// array.
+// Ascending bitonic sort of 32 * E values held E per lane, element index lane * E + e: partners closer than E
+// sit in the same lane's registers, farther ones in lane ^ (j / E).
+template <int E>
+__device__ __forceinline__ void warp_sort_regs(uint32_t (&v)[E], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & j) == 0) {
+                        const bool up = ((lane * E + e) & k) == 0;
+                        const uint32_t a = v[e], b = v[e + j];
+                        v[e] = up ? min(a, b) : max(a, b);
+                        v[e + j] = up ? max(a, b) : min(a, b);
+                    }
+                }
+            } else {
+                const int lj = j / E;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, v[e], lj);
+                    const bool up = ((lane * E + e) & k) == 0, low = (lane & lj) == 0;
+                    v[e] = (up == low) ? min(v[e], y) : max(v[e], y);
+                }
+            }
+        }
+    }
+}
+
+// Load up to 32 * E slots of a row into registers, sort them, store them back.
+template <int E>
+__device__ __forceinline__ void sort_row_regs(uint32_t* v, uint32_t m, int lane) {
+    uint32_t x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)(lane * E + e);
+        x[e] = (i < m) ? v[i] : 0xffffffffu;
+    }
+    warp_sort_regs<E>(x, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t i = (uint32_t)(lane * E + e);
+        if (i < m) v[i] = x[e];
+    }
+}
+
+// Segment sort, pass 2: one warp per listed row: up to 256 slots in registers (bitonic, shuffles across lanes),
+// up to kSegSmem with a bitonic sort in shared memory, longer ones by rank (every slot counts the smaller ones;
+// slot ids are distinct) through the scratch array.
 __global__ void __launch_bounds__(kSegWarps * 32) det_segsort_long_kernel(const uint32_t* __restrict__ rowptr,
                                                                           const uint32_t* __restrict__ longrows,
                                                                           const uint32_t* __restrict__ nlong,
@@ -312,6 +360,12 @@ __global__ void __launch_bounds__(kSegWarps * 32) det_segsort_long_kernel(const 
             uint32_t x = ((uint32_t)lane < m) ? v[lane] : 0xffffffffu;
             x = warp_sort32(x, lane);
             if ((uint32_t)lane < m) v[lane] = x;
+        } else if (m <= 64u) {
+            sort_row_regs<2>(v, m, lane);
+        } else if (m <= 128u) {
+            sort_row_regs<4>(v, m, lane);
+        } else if (m <= 256u) {
+            sort_row_regs<8>(v, m, lane);
         } else if (m <= (uint32_t)kSegSmem) {
             uint32_t p2 = 64u;
             while (p2 < m) p2 <<= 1;
