@@ -12,9 +12,11 @@
 //   dv_s = H_s * sum over the team of w_g (ax (d10 - d00) + fx (d11 - d01))
 // (the exact adjoint of the forward's bilinear sample, as in bwd.cu).  dw is
 // stored at once; the two team sums wait in shared memory and dloc of a point
-// is their sum, scaled by W_s and H_s, in scale order at the end.  A point-scale that is not listed gets
-// dw = 0, a point with no listed scale dloc = 0.  Every sum has a fixed
-// order, so the result is bitwise reproducible.
+// is their sum, scaled by W_s and H_s, in scale order at the end.  A
+// point-scale that is not listed gets dw = 0, a point with no listed scale
+// dloc = 0.  Every sum has a fixed order, so the result is bitwise
+// reproducible.  An anchor whose locations and sums do not fit in shared
+// memory falls back to the per-point kernel of bwd.cu without its scatter.
 #include "common.cuh"
 #include "internal.h"
 #include "units.cuh"
