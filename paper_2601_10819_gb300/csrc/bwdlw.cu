@@ -51,8 +51,24 @@ struct LocWSmem {
     }
 };
 
+// Sums over `width` lanes (a power of two up to 32), two values at once: the steps are unrolled, so the two
+// chains of shuffles interleave.  The steps run from the widest down, the same order as a loop over
+// off = width/2, ..., 1, so the sums are bitwise those of one value at a time.
+__device__ __forceinline__ void team_sum2_lw(float& a, float& b, unsigned mask, int width) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        if (off < width) {
+            const float ta = __shfl_xor_sync(mask, a, off), tb = __shfl_xor_sync(mask, b, off);
+            a += ta;
+            b += tb;
+        }
+    }
+}
+
 __device__ __forceinline__ float team_sum_lw(float v, unsigned mask, int width) {
-    for (int off = width >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        if (off < width) v += __shfl_xor_sync(mask, v, off);
     return v;
 }
 
@@ -157,8 +173,9 @@ __global__ void __launch_bounds__(256, NV == 2 ? 3 : (NV == 1 ? 4 : 2)) bwd_locw
             const float dwp = ax * ay * d00 + r.fx * ay * d01 + ax * r.fy * d10 + r.fx * r.fy * d11;
             const float dw = team_sum_lw(dwp, tmask, lg);
             if ((tl & (lg - 1)) == 0) gwb[(long long)ps * p.G + g] = dw;
-            const float du = team_sum_lw(wv * (ay * (d01 - d00) + r.fy * (d11 - d10)), tmask, p.rt);
-            const float dv = team_sum_lw(wv * (ax * (d10 - d00) + r.fx * (d11 - d01)), tmask, p.rt);
+            float du = wv * (ay * (d01 - d00) + r.fy * (d11 - d10));
+            float dv = wv * (ax * (d10 - d00) + r.fx * (d11 - d01));
+            team_sum2_lw(du, dv, tmask, p.rt);
             if (tl == 0) suv[ps] = make_float2(du, dv);  // scaled by W_s, H_s at the end
         }
         __syncthreads();  // the list is rebuilt for the next chunk; suv is complete after the last one
