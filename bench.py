@@ -659,8 +659,15 @@ def main():
     t_l2_fwd = cnt.fwd_l2_gather_bytes / (l2_gather_gbs * 1e9) * 1e6
     t_hbm_bwd = cnt.bwd_hbm_bytes / (hbm_peak * 1e9) * 1e6
     red_bytes = cnt.bwd_l2_bytes - cnt.fwd_l2_gather_bytes
-    t_gather_bwd = cnt.fwd_l2_gather_bytes / (l2_gather_gbs * 1e9) * 1e6
-    t_red_bwd = red_bytes / (l2_red_gbs * 1e9) * 1e6
+    if det:
+        # the deterministic backward reduces nothing in L2: it gathers the corner rows (dloc, dw) and, per
+        # in-bound corner, its anchor's FP32 grad_out row (the same bytes the atomic form reduces)
+        bwd_gather_bytes = cnt.fwd_l2_gather_bytes + red_bytes
+        t_red_bwd = 0.0
+    else:
+        bwd_gather_bytes = cnt.fwd_l2_gather_bytes
+        t_red_bwd = red_bytes / (l2_red_gbs * 1e9) * 1e6
+    t_gather_bwd = bwd_gather_bytes / (l2_gather_gbs * 1e9) * 1e6
     t_roof_bwd = max(t_hbm_bwd, t_gather_bwd, t_red_bwd)
     line = {
         "metric": METRIC, "value": us_per_frame, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -684,6 +691,9 @@ def main():
                      "binding": ({"resource": "L2 FP32 vector reductions (msda_probe_reduce)",
                                   "achieved": red_bytes / (bwd_ms * 1e-3) / 1e9, "peak": l2_red_gbs, "unit": "GB/s",
                                   "frac": t_red_bwd / (bwd_ms * 1e3)} if dom == "msda_backward" and not det else
+                                 {"resource": "L2 random-row gathers (msda_probe_read): corner rows and grad_out rows",
+                                  "achieved": bwd_gather_bytes / (bwd_ms * 1e-3) / 1e9, "peak": l2_gather_gbs,
+                                  "unit": "GB/s", "frac": t_gather_bwd / (bwd_ms * 1e3)} if dom == "msda_backward" else
                                  {"resource": "L2 random-row gathers (msda_probe_read)",
                                   "achieved": cnt.fwd_l2_gather_bytes / (fwd_ms * 1e-3) / 1e9, "peak": l2_gather_gbs,
                                   "unit": "GB/s", "frac": t_l2_fwd / (fwd_ms * 1e3)} if dom == "msda_forward" else
