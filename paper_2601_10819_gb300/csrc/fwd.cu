@@ -161,8 +161,8 @@ __device__ __forceinline__ void accumulate_anchor(const FT* __restrict__ fb, con
 }
 
 // ---------------------------------------------------------------------------
-// Two-stage form of accumulate_anchor (tuning variant 4).  The anchor's
-// point-scales (camera, keypoint, scale) are taken in chunks of
+// Two-stage form of accumulate_anchor (the default; variant 4 is the other).
+// The anchor's point-scales (camera, keypoint, scale) are taken in chunks of
 // kUnitsPerThread per thread: stage A culls each one and locates its cell
 // once (instead of once in each of a team's lanes) and compacts the in-view
 // ones, in order, into a list in shared memory; stage B deals the list
