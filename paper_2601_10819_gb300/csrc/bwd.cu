@@ -58,8 +58,8 @@ __device__ __forceinline__ float team_sum(float v, unsigned mask, int width) {
     return v;
 }
 
-// SCATTER = false builds the form without the feature-gradient reductions (the deterministic modes take
-// dloc and dw from it), which needs fewer registers.
+// SCATTER = false builds the form without the feature-gradient reductions (dloc and dw of the deterministic
+// modes for anchors too large for bwdlw.cu), which needs fewer registers.
 template <typename FT, typename WT, int NV, bool SCATTER>
 __global__ void __launch_bounds__(256) bwd_atomic_kernel(const BwdArgs p) {
     constexpr int VEC = Elem<FT>::VEC;
