@@ -35,6 +35,14 @@
  *   and sum is FP32; a BF16/FP16 output is rounded once, to nearest even.
  * - Alignment: every tensor pointer must be 16-byte aligned, and
  *   (C/G) * sizeof(feat element) must be a multiple of 16 bytes.
+ * - Channel split: a channel row is read by a team of lanes, each lane
+ *   taking n 16-byte vectors (VEC = 16 / sizeof(feat element) channels per
+ *   vector).  Some n in {1, 2, 4} must give C % (VEC*n) == 0,
+ *   (C/G) % (VEC*n) == 0 and a team size C / (VEC*n) that is a power of two
+ *   no larger than 32; otherwise the call returns MSDA_ERR_UNSUPPORTED.
+ *   For example C=256 works for every G that divides it into groups of at
+ *   least 16 bytes, while C=96 with G=2 (FP32), C=48 with G=3 (BF16) and FP32
+ *   rows wider than 512 channels are rejected.
  * - Every map must satisfy H >= 1, W >= 1 and start + H*W <= sum_hw.  The
  *   shape tables live on the device, so they are checked by the kernels: a
  *   bad map is skipped (it contributes nothing) and the device status word

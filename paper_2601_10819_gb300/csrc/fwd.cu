@@ -753,7 +753,10 @@ msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int
 // different streams without ordering) race and give wrong results.
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocMaxScenes = 1024;
-static __device__ __align__(256) unsigned int g_batched_noalloc_scratch[kNoAllocMaxScenes + 1];
+// Sized from the batched forward's own workspace rule (one counter per scene plus the work counter, rounded
+// up to 256 bytes), so every scene count up to the limit passes its workspace check.
+constexpr size_t kNoAllocScratchBytes = ((sizeof(unsigned int) * (kNoAllocMaxScenes + 1) + 255) / 256) * 256;
+static __device__ __align__(256) unsigned int g_batched_noalloc_scratch[kNoAllocScratchBytes / sizeof(unsigned int)];
 
 int batched_noalloc_max_scenes() { return kNoAllocMaxScenes; }
 
@@ -782,6 +785,9 @@ msda_status launch_forward_batched_noalloc(const msda_scene* scenes, int num_sce
         }
         scratch = addr[dev];
     }
+    if (batched_workspace(num_scenes) > sizeof(g_batched_noalloc_scratch))
+        return fail(MSDA_ERR_INVALID_ARG, "msda_forward_batched_noalloc: %d scenes exceed the built-in limit of %d",
+                    num_scenes, kNoAllocMaxScenes);
     return launch_forward_batched(scenes, num_scenes, total_anchors, max_ncam, Nscale, C, P, G, ft, wt, ot,
                                   scratch, sizeof(g_batched_noalloc_scratch), done_ns, warps, blocks_per_sm, vec,
                                   stream);

@@ -84,6 +84,18 @@ def test_reduced_precision_output_is_rounded_fp32(odt, ws):
 HETERO = [[(5, 7), (3, 4), (2, 2)], [(9, 4), (4, 2), (1, 1)], [(6, 13), (3, 7), (2, 3)]]
 
 
+def split_supported(C, G, fdt):
+    """The channel-split rule stated in include/msda.h."""
+    vec = 16 // (4 if fdt == "f32" else 2)
+    for n in (1, 2, 4):
+        cpl = vec * n
+        if C % cpl == 0 and (C // G) % cpl == 0:
+            r = C // cpl
+            if r <= 32 and r & (r - 1) == 0:
+                return True
+    return False
+
+
 @pytest.mark.parametrize("ws", PATHS)
 @pytest.mark.parametrize("C,G,fdt", [(32, 4, "f32"), (64, 4, "f32"), (64, 8, "bf16"), (128, 2, "bf16"),
                                      (512, 8, "bf16"), (1024, 8, "bf16"), (96, 2, "f32"), (48, 3, "bf16"),
@@ -92,11 +104,13 @@ def test_channel_splits_and_ragged_maps(C, G, fdt, ws):
     gen = torch.Generator().manual_seed(C * 7 + G)
     pr = inputs.make_problem(gen, B=2, cam_maps=HETERO, C=C, G=G, A=37, P=5, loc_range=(-0.3, 1.3),
                              feat_dtype=fdt, w_dtype=fdt, with_grad=False)
-    try:
-        out = gpu_forward(pr, workspace=ws)
-    except msda.MSDAError as e:
-        assert e.code == 2 and (C // G) * (4 if fdt == "f32" else 2) % 16 == 0
-        pytest.skip(f"unsupported split reported: {e}")
+    if not split_supported(C, G, fdt):
+        # the header's channel-split rule rejects this split: the call must say so, not compute
+        with pytest.raises(msda.MSDAError) as e:
+            gpu_forward(pr, workspace=ws)
+        assert e.value.code == 2
+        return
+    out = gpu_forward(pr, workspace=ws)
     tol = TOL_FP32 if fdt == "f32" else TOL_LOWP_OUT
     assert relerr(out.cpu().double().numpy(), oracle_forward(pr)) <= tol
 

@@ -63,3 +63,27 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls():
         t = plan.done_ns.cpu()
         assert t[0] > 0 and torch.all(t[1:] >= t[0])
     assert msda.device_status() == 0
+
+
+@pytest.mark.gpu
+def test_noalloc_at_its_scene_limit_matches_workspace_entry_point():
+    """Exactly the advertised number of scenes (tiny ones: 1 camera, 1 anchor each) must run."""
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    lib = _declare(ensure_lib())
+    limit = lib.msda_forward_batched_noalloc_max_scenes()
+    gen = torch.Generator().manual_seed(22)
+    scenes = [inputs.make_problem(gen, B=1, cam_maps=[[(4, 6), (2, 3)]], C=32, G=4, A=1, P=2,
+                                  loc_range=(-0.1, 1.1), with_grad=False).to("cuda") for _ in range(limit)]
+    plan = msda.plan_batched(scenes)
+    ref = [o.clone() for o in plan.run()]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream().cuda_stream
+    for o in plan.outs:
+        o.fill_(float("nan"))
+    plan.done_ns.zero_()
+    assert _call_noalloc(lib, plan, stream) == 0, lib.msda_last_error().decode()
+    torch.cuda.synchronize()
+    got = torch.stack(plan.outs).cpu().double()
+    want = torch.stack(ref).cpu().double()
+    assert torch.equal(got, want)  # same kernel, same launch: bitwise equal
+    assert msda.device_status() == 0
