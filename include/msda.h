@@ -99,7 +99,9 @@ typedef struct {
                               point-scale once into a shared list; also for
                               msda_forward_train and _oae);
                               msda_backward (deterministic):
-                              2 = staged camera-group form                   */
+                              2 = staged camera-group form,
+                              5 = corner-slot form even where the
+                              cell-binned form applies                       */
     int vectors_per_lane;  /* 16-byte feature vectors per lane and corner row
                               (1, 2 or 4): more work per lane, fewer lanes
                               per point; 0 = built-in default (2 when that
@@ -221,9 +223,18 @@ msda_status msda_keypoints(const float* anchors, const float* offsets, const flo
  *     counter strictly in camera order, which keeps the rows being
  *     accumulated in L2; with workspace = NULL a static stride is used.
  *   deterministic = 1: no floating-point atomics; bitwise reproducible.  By
- *     default the corner contributions are grouped by feature row (a
- *     counting sort whose integer counters place them), each row's group is
- *     sorted by slot id, and each row is reduced in that order.  With
+ *     default (cell-binned form) each map's in-view point-scales are binned
+ *     by bilinear cell in point order, and every feature row is summed over
+ *     the bins of its four neighbouring cells in a fixed order, with
+ *     grad_out of one channel group staged in shared memory.  It applies
+ *     when the valid maps do not overlap, A*P <= 65535, C/G is 4 times a
+ *     power of two up to 128, Ncam*Nscale <= 4096, A*(C/G)*4 bytes fit in a
+ *     block's shared memory and every map's (H+1)*(W+1) cells fit the
+ *     binning block; the map conditions are checked on the device.
+ *     Otherwise (or with tuning->variant = 5) the corner-slot form runs:
+ *     the corner contributions are grouped by feature row (a counting sort
+ *     whose integer counters place them), each row's group is sorted by
+ *     slot id, and each row is reduced in that order.  With
  *     tuning->variant = 2, when the staged kernels apply (Nscale <= 4, C/G a
  *     power of two in 4..128, at most 40960 bilinear cells per map, maps
  *     that do not overlap, A*(C/G)*4 bytes of grad_out per group fitting in

@@ -290,8 +290,9 @@ msda_status msda_backward(const void* feat, msda_dtype feat_dtype, const int32_t
         if (staged && cg_supported(p))
             return launch_backward_cg(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes,
                                       (cudaStream_t)stream);
+        const bool cells = !(tuning && tuning->variant == 5);  // variant 5: the corner-slot form
         return launch_backward_det(p, grad_out, grad_feat, grad_loc, grad_weights, workspace, workspace_bytes,
-                                   warps, (cudaStream_t)stream);
+                                   warps, cells, (cudaStream_t)stream);
     }
     if (workspace && !aligned16(workspace))
         return fail(MSDA_ERR_WORKSPACE, "msda_backward: workspace must be 16-byte aligned");

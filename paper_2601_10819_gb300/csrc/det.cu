@@ -21,6 +21,7 @@
 // arithmetic as every other kernel, so keys and weights agree.
 #include "common.cuh"
 #include "internal.h"
+#include "wsort.cuh"
 
 namespace msda {
 
@@ -38,12 +39,12 @@ struct DetLayout {
     size_t vals, e_om, e_pt, e_ba, cnt, rowptr, tsum, total;
 };
 
-static DetLayout det_layout(long long npts, long long nrows) {
+static DetLayout det_layout(long long npts, long long nrows, size_t base = 0) {
     DetLayout L;
     L.n = (size_t)npts * 4;
     L.nrows = (size_t)nrows;
     L.ntiles = (int)((nrows + kRowTile - 1) / kRowTile);
-    size_t off = 0;
+    size_t off = base;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     L.vals = take(4 * L.n);   // slot ids grouped by row (sorted within each row)
     L.e_om = take(4 * L.n);   // flat arrays per contribution; e_om is also the large-segment sort's scratch
@@ -56,9 +57,24 @@ static DetLayout det_layout(long long npts, long long nrows) {
     return L;
 }
 
+// The corner-slot arrays start after the cell-binned path's plan area when that path can apply (its flag
+// gates these kernels); both paths' arrays then share the rest of the workspace.
+static size_t det_body_base(const Problem& p) { return cb_shape_ok(p) ? cb_plan_bytes(p) : 0; }
+
 size_t backward_det_workspace(const Problem& p) {
     const long long npts = (long long)p.B * p.A * p.P * p.Ncam * p.Nscale;
-    return det_layout(npts, (long long)p.B * p.sum_hw).total;
+    const size_t base = det_body_base(p);
+    const size_t slots = det_layout(npts, (long long)p.B * p.sum_hw, base).total;
+    const size_t cells = cb_shape_ok(p) ? cb_workspace(p, base) : 0;
+    return slots > cells ? slots : cells;
+}
+
+// True when the cell-binned path ran and set its flag: the corner-slot kernels have nothing to do.
+__device__ __forceinline__ bool gated(const int* gate) { return gate && *reinterpret_cast<const volatile int*>(gate); }
+
+__global__ void __launch_bounds__(256) det_zero_kernel(uint32_t* __restrict__ p, long long n, const int* gate) {
+    if (gated(gate)) return;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) p[i] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -74,6 +90,8 @@ struct KeyArgs {
     const uint32_t* rowptr;  // row offsets (fill pass)
     uint32_t* vals;          // slot ids grouped by row (fill pass)
     int* status;
+    const int* gate;         // the cell-binned path's flag, or NULL
+    long long nblk;          // point-scale blocks of kKeyBlock
 };
 
 // Division by a fixed d >= 1 for numerators below 2^31 (the round-up method
@@ -162,7 +180,9 @@ __device__ __forceinline__ unsigned corner_keys(const KeyArgs& a, long long pt, 
 // never runs out of places; the check only keeps a store inside the row if they ever differed.
 template <bool FILL>
 __global__ void __launch_bounds__(256) det_rows_kernel(const KeyArgs a) {
-    const long long base = (long long)blockIdx.x * kKeyBlock + (long long)threadIdx.x * kKeyPts;
+    if (gated(a.gate)) return;
+    for (long long blk = blockIdx.x; blk < a.nblk; blk += gridDim.x) {
+    const long long base = blk * kKeyBlock + (long long)threadIdx.x * kKeyPts;
 #pragma unroll
     for (int i = 0; i < kKeyPts; ++i) {
         const long long pt = base + i;
@@ -185,13 +205,15 @@ __global__ void __launch_bounds__(256) det_rows_kernel(const KeyArgs a) {
             }
         }
     }
+    }
 }
 
 // Row offsets, step 1: per tile of kRowTile rows, the exclusive prefix of the counts inside the tile, and the
 // tile's total.
 __global__ void __launch_bounds__(1024) row_scan_tile_kernel(const uint32_t* __restrict__ cnt, long long nrows,
                                                              uint32_t* __restrict__ rowptr,
-                                                             uint32_t* __restrict__ tsum) {
+                                                             uint32_t* __restrict__ tsum, const int* gate) {
+    if (gated(gate)) return;
     __shared__ uint32_t ws[32];
     const long long r0 = (long long)blockIdx.x * kRowTile + (long long)threadIdx.x * 4;
     uint32_t v[4], s = 0u;
@@ -212,7 +234,8 @@ __global__ void __launch_bounds__(1024) row_scan_tile_kernel(const uint32_t* __r
 
 // Step 2 (one block): the tile totals become their exclusive prefix; *total gets the number of corners.
 __global__ void __launch_bounds__(1024) row_scan_totals_kernel(uint32_t* __restrict__ tsum, int ntiles,
-                                                               uint32_t* __restrict__ total) {
+                                                               uint32_t* __restrict__ total, const int* gate) {
+    if (gated(gate)) return;
     __shared__ uint32_t ws[32];
     uint32_t carry = 0u;
     for (int base = 0; base < ntiles; base += 1024) {
@@ -228,7 +251,9 @@ __global__ void __launch_bounds__(1024) row_scan_totals_kernel(uint32_t* __restr
 
 // Step 3: each row offset gets its tile's prefix.
 __global__ void __launch_bounds__(256) row_scan_add_kernel(uint32_t* __restrict__ rowptr,
-                                                           const uint32_t* __restrict__ tsum, long long nrows) {
+                                                           const uint32_t* __restrict__ tsum, long long nrows,
+                                                           const int* gate) {
+    if (gated(gate)) return;
     for (long long r = (long long)blockIdx.x * 256 + threadIdx.x; r < nrows; r += (long long)gridDim.x * 256)
         rowptr[r] += tsum[r / kRowTile];
 }
@@ -239,7 +264,8 @@ __global__ void __launch_bounds__(256) row_scan_add_kernel(uint32_t* __restrict_
 __global__ void __launch_bounds__(256) det_segsort_short_kernel(const uint32_t* __restrict__ rowptr,
                                                                 long long nrows, uint32_t* __restrict__ vals,
                                                                 uint32_t* __restrict__ longrows,
-                                                                uint32_t* __restrict__ nlong) {
+                                                                uint32_t* __restrict__ nlong, const int* gate) {
+    if (gated(gate)) return;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long end = (nrows + 31) & ~31ll;  // whole warps iterate together
@@ -278,51 +304,6 @@ __global__ void __launch_bounds__(256) det_segsort_short_kernel(const uint32_t* 
     }
 }
 
-// Ascending bitonic sort of one value per lane across the warp.
-__device__ __forceinline__ uint32_t warp_sort32(uint32_t x, int lane) {
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
-            const bool up = (lane & k) == 0, low = (lane & j) == 0;
-            x = (up == low) ? min(x, y) : max(x, y);
-        }
-    }
-    return x;
-}
-
-// Ascending bitonic sort of 32 * E values held E per lane, element index lane * E + e: partners closer than E
-// sit in the same lane's registers, farther ones in lane ^ (j / E).
-template <int E>
-__device__ __forceinline__ void warp_sort_regs(uint32_t (&v)[E], int lane) {
-#pragma unroll
-    for (int k = 2; k <= 32 * E; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j < E) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    if ((e & j) == 0) {
-                        const bool up = ((lane * E + e) & k) == 0;
-                        const uint32_t a = v[e], b = v[e + j];
-                        v[e] = up ? min(a, b) : max(a, b);
-                        v[e + j] = up ? max(a, b) : min(a, b);
-                    }
-                }
-            } else {
-                const int lj = j / E;
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const uint32_t y = __shfl_xor_sync(0xffffffffu, v[e], lj);
-                    const bool up = ((lane * E + e) & k) == 0, low = (lane & lj) == 0;
-                    v[e] = (up == low) ? min(v[e], y) : max(v[e], y);
-                }
-            }
-        }
-    }
-}
-
 // Load up to 32 * E slots of a row into registers, sort them, store them back.
 template <int E>
 __device__ __forceinline__ void sort_row_regs(uint32_t* v, uint32_t m, int lane) {
@@ -347,7 +328,9 @@ __global__ void __launch_bounds__(kSegWarps * 32) det_segsort_long_kernel(const 
                                                                           const uint32_t* __restrict__ longrows,
                                                                           const uint32_t* __restrict__ nlong,
                                                                           uint32_t* __restrict__ vals,
-                                                                          uint32_t* __restrict__ scratch) {
+                                                                          uint32_t* __restrict__ scratch,
+                                                                          const int* gate) {
+    if (gated(gate)) return;
     __shared__ uint32_t sbuf[kSegWarps][kSegSmem];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* buf = sbuf[warp];
@@ -423,6 +406,8 @@ struct RedArgs {
     int sum_hw, C, Ncam, Nscale, A, P, G, Cg, rt, sbits;
     FastDiv ncam, pncam;  // divisions by Ncam and P*Ncam
     int* status;
+    const int* gate;      // the cell-binned path's flag, or NULL
+    long long nrb;        // row blocks of the reduce
 };
 
 // Per sorted contribution e (in key order, valid keys only): decode the slot, recompute the corner weight
@@ -430,6 +415,7 @@ struct RedArgs {
 // reduce reads them contiguously instead of chasing slot -> location -> cell for every contribution.
 __global__ void __launch_bounds__(256) det_prep_kernel(RedArgs a, size_t n, float* om_out, uint32_t* pt_out,
                                                        uint32_t* ba_out) {
+    if (gated(a.gate)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     MapInfo* smap = reinterpret_cast<MapInfo*>(smem);
     const int nmaps = a.Ncam * a.Nscale;
@@ -461,14 +447,16 @@ __global__ void __launch_bounds__(256) det_prep_kernel(RedArgs a, size_t n, floa
 template <typename WT, int CPL>
 __global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
     constexpr int U = CPL >= 32 ? 1 : 32 / CPL;
+    if (gated(a.gate)) return;
     const int tpw = 32 / a.rt;
     const int nteams = (blockDim.x >> 5) * tpw;
     const int lane = threadIdx.x & 31;
     const int team = (threadIdx.x >> 5) * tpw + lane / a.rt;
     const int c0 = (lane & (a.rt - 1)) * CPL;
     const int g = c0 / a.Cg;
-    const long long row = (long long)blockIdx.x * nteams + team;
-    if (row >= a.nrows) return;
+    for (long long rb = blockIdx.x; rb < a.nrb; rb += gridDim.x) {
+    const long long row = rb * nteams + team;
+    if (row >= a.nrows) continue;
     const WT* wp = reinterpret_cast<const WT*>(a.w);
     float acc[CPL];
 #pragma unroll
@@ -509,6 +497,7 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
     float4* dst = reinterpret_cast<float4*>(a.gfeat + row * a.C + c0);
 #pragma unroll
     for (int j = 0; j < CPL / 4; ++j) dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+    }
 }
 
 using RedKernel = void (*)(const RedArgs);
@@ -526,7 +515,7 @@ static RedKernel red_pick(int cpl) {
 
 msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
                                 float* grad_loc, float* grad_w, void* ws, size_t ws_bytes,
-                                int warps, cudaStream_t stream) {
+                                int warps, bool allow_cells, cudaStream_t stream) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);
     if (st != MSDA_OK) return st;
@@ -536,9 +525,11 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     const long long npoints = (long long)p.B * p.A * p.P * p.Ncam;
     if (npts * 4 >= (1ll << 32) || (npoints << (sbits + 2)) >= (1ll << 31) || nrows >= (1ll << 32) - 1)
         return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: deterministic mode limited to 2^31 corner slots and 2^32 rows");
-    const DetLayout L = det_layout(npts, nrows);
-    if (!ws || ws_bytes < L.total)
-        return fail(MSDA_ERR_WORKSPACE, "msda_backward: deterministic mode needs %zu workspace bytes", L.total);
+    const size_t body = det_body_base(p);
+    const DetLayout L = det_layout(npts, nrows, body);
+    const size_t need = backward_det_workspace(p);
+    if (!ws || ws_bytes < need)
+        return fail(MSDA_ERR_WORKSPACE, "msda_backward: deterministic mode needs %zu workspace bytes", need);
     // The row reduce has its own lane split, independent of the gather kernel's: 8 channels per lane when C
     // and the group width allow it (measured fastest: short rows of ~10 contributions favour many lanes),
     // else the split of the gather kernel.
@@ -560,6 +551,14 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     if (st != MSDA_OK) return st;
     if (nrows == 0) return MSDA_OK;
 
+    // The feature gradient: the cell-binned path when it applies (decided on the device for the maps; its
+    // flag then turns the corner-slot kernels below into empty launches), else the corner-slot path.
+    const int* gate = nullptr;
+    if (allow_cells && cb_shape_ok(p) && cb_device_ok(p, dev)) {
+        if ((st = launch_backward_cb(p, grad_out, grad_feat, ws, body, stream)) != MSDA_OK) return st;
+        gate = reinterpret_cast<const int*>(ws);
+    }
+
     unsigned char* base = reinterpret_cast<unsigned char*>(ws);
     uint32_t* vals = reinterpret_cast<uint32_t*>(base + L.vals);
     uint32_t* e_om = reinterpret_cast<uint32_t*>(base + L.e_om);
@@ -571,28 +570,33 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     KeyArgs ka;
     ka.shape = p.shape; ka.start = p.start; ka.loc = p.loc; ka.npts = npts; ka.sum_hw = p.sum_hw; ka.A = p.A;
     ka.P = p.P; ka.Ncam = p.Ncam; ka.Nscale = p.Nscale; ka.sbits = sbits; ka.cnt = cnt; ka.rowptr = rowptr;
-    ka.vals = vals; ka.status = dev.status;
+    ka.vals = vals; ka.status = dev.status; ka.gate = gate;
     const long long nkb = (npts + kKeyBlock - 1) / kKeyBlock;
+    ka.nblk = nkb;
+    const long long kgrid = nkb < (long long)dev.sm_count * 8 ? nkb : (long long)dev.sm_count * 8;
     // per-row counts of the in-bound corners, row offsets (three-step scan), then the slot ids in place
-    if (cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(nrows + 1), stream) != cudaSuccess)
-        return check_launch("msda_backward memset");
-    if (nkb > 0) det_rows_kernel<false><<<(unsigned)nkb, 256, 0, stream>>>(ka);
-    row_scan_tile_kernel<<<(unsigned)L.ntiles, 1024, 0, stream>>>(cnt, nrows, rowptr, tsum);
-    row_scan_totals_kernel<<<1, 1024, 0, stream>>>(tsum, L.ntiles, rowptr + nrows);
+    {
+        long long zb = (nrows + 1 + 255) / 256;
+        if (zb > (long long)dev.sm_count * 8) zb = (long long)dev.sm_count * 8;
+        det_zero_kernel<<<(unsigned)zb, 256, 0, stream>>>(cnt, nrows + 1, gate);
+    }
+    if (nkb > 0) det_rows_kernel<false><<<(unsigned)kgrid, 256, 0, stream>>>(ka);
+    row_scan_tile_kernel<<<(unsigned)L.ntiles, 1024, 0, stream>>>(cnt, nrows, rowptr, tsum, gate);
+    row_scan_totals_kernel<<<1, 1024, 0, stream>>>(tsum, L.ntiles, rowptr + nrows, gate);
     {
         long long ab = (nrows + 255) / 256;
         if (ab > (long long)dev.sm_count * 16) ab = (long long)dev.sm_count * 16;
-        row_scan_add_kernel<<<(unsigned)ab, 256, 0, stream>>>(rowptr, tsum, nrows);
+        row_scan_add_kernel<<<(unsigned)ab, 256, 0, stream>>>(rowptr, tsum, nrows, gate);
     }
     if ((st = check_launch("msda_backward row offsets")) != MSDA_OK) return st;
     if (nkb > 0) {
-        det_rows_kernel<true><<<(unsigned)nkb, 256, 0, stream>>>(ka);
+        det_rows_kernel<true><<<(unsigned)kgrid, 256, 0, stream>>>(ka);
         // the per-row counts are all zero again after the fill: their array takes the list of long rows
         long long sb = (nrows + 255) / 256;
         if (sb > (long long)dev.sm_count * 16) sb = (long long)dev.sm_count * 16;
-        det_segsort_short_kernel<<<(unsigned)sb, 256, 0, stream>>>(rowptr, nrows, vals, cnt, cnt + nrows);
+        det_segsort_short_kernel<<<(unsigned)sb, 256, 0, stream>>>(rowptr, nrows, vals, cnt, cnt + nrows, gate);
         det_segsort_long_kernel<<<(unsigned)dev.sm_count * 8, kSegWarps * 32, 0, stream>>>(rowptr, cnt, cnt + nrows,
-                                                                                          vals, e_om);
+                                                                                          vals, e_om, gate);
         if ((st = check_launch("msda_backward row groups")) != MSDA_OK) return st;
     }
     RedArgs ra;
@@ -603,7 +607,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     ra.e_ba = e_ba;
     ra.wide = (((uintptr_t)grad_out % 32) == 0 && ((size_t)p.C * 4) % 32 == 0) ? 1 : 0;
     ra.sum_hw = p.sum_hw; ra.C = p.C; ra.Ncam = p.Ncam; ra.Nscale = p.Nscale; ra.A = p.A; ra.P = p.P;
-    ra.G = p.G; ra.Cg = p.Cg; ra.rt = red_rt; ra.sbits = sbits; ra.status = dev.status;
+    ra.G = p.G; ra.Cg = p.Cg; ra.rt = red_rt; ra.sbits = sbits; ra.status = dev.status; ra.gate = gate;
     ra.ncam = make_fastdiv((uint32_t)(p.Ncam > 0 ? p.Ncam : 1));
     ra.pncam = make_fastdiv((uint32_t)((long long)p.P * p.Ncam > 0 ? (long long)p.P * p.Ncam : 1));
     const size_t smem = sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale;
@@ -615,8 +619,9 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
         if ((st = check_launch("msda_backward prep")) != MSDA_OK) return st;
     }
     const int nteams = 8 * (32 / red_rt);
-    const long long rblocks = (nrows + nteams - 1) / nteams;
-    red<<<(unsigned)rblocks, 256, 0, stream>>>(ra);
+    ra.nrb = (nrows + nteams - 1) / nteams;
+    const long long rgrid = ra.nrb < (long long)dev.sm_count * 8 ? ra.nrb : (long long)dev.sm_count * 8;
+    red<<<(unsigned)rgrid, 256, 0, stream>>>(ra);
     return check_launch("msda_backward reduce");
 }
 

@@ -66,9 +66,20 @@ msda_status launch_backward_loc_w(const Problem& p, const float* grad_out, float
 msda_status launch_backward_locw(const Problem& p, const float* grad_out, float* grad_loc, float* grad_w, int warps,
                                  cudaStream_t stream);
 size_t backward_det_workspace(const Problem& p);
+// allow_cells: take the cell-binned feature gradient (cb.cu) where it applies; false forces the corner-slot
+// path of det.cu.
 msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
                                 float* grad_loc, float* grad_w, void* ws, size_t ws_bytes,
-                                int warps, cudaStream_t stream);
+                                int warps, bool allow_cells, cudaStream_t stream);
+// The cell-binned deterministic feature gradient (cb.cu).  cb_shape_ok: the sizes allow it on any device;
+// cb_device_ok: and on the current one.  Its plan area (cb_plan_bytes) opens the workspace; its other arrays
+// start at body_base.
+bool cb_shape_ok(const Problem& p);
+bool cb_device_ok(const Problem& p, const DeviceInfo& dev);
+size_t cb_plan_bytes(const Problem& p);
+size_t cb_workspace(const Problem& p, size_t body_base);
+msda_status launch_backward_cb(const Problem& p, const float* grad_out, float* grad_feat, void* ws,
+                               size_t body_base, cudaStream_t stream);
 size_t batched_workspace(int num_scenes);
 msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int total_anchors,
                                    int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,

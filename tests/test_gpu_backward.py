@@ -34,8 +34,9 @@ def check_against_oracle(pr, grads, tol, label=""):
     return errs
 
 
-# (deterministic, variant): atomic scatter, row-grouped deterministic, staged deterministic
-MODES = [(False, 0), (True, 0), (True, 2)]
+# (deterministic, variant): atomic scatter, deterministic (cell-binned where it applies), staged deterministic,
+# deterministic corner-slot form
+MODES = [(False, 0), (True, 0), (True, 2), (True, 5)]
 
 
 @pytest.mark.parametrize("det,variant", MODES)
@@ -71,7 +72,7 @@ def test_ragged_maps_and_splits(C, G, fdt, det, variant):
     check_against_oracle(pr, gpu_backward(pr, det, None, variant), tol, f"ragged C={C} G={G} {fdt} det={det}/{variant}")
 
 
-@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("variant", [0, 2, 5])
 def test_deterministic_mode_is_bitwise_reproducible(variant):
     pr = inputs.make_workload(2, ncam=8)
     a = gpu_backward(pr, True, 8, variant)
@@ -104,7 +105,7 @@ def test_outside_in_64cam_full_backward():
         e = relerr(g.double().numpy(), r)
         print(f"outside-in-64cam {name} rel err {e:.2e}")
         assert e <= TOL_LOWP_GRAD
-    for variant in (0, 2):
+    for variant in (0, 2, 5):
         gd = gpu_backward(pr, True, None, variant)
         for g, r, name in zip(gd, ref, ["dfeat", "dloc", "dw"]):
             e = relerr(g.double().numpy(), r)
@@ -395,8 +396,9 @@ def test_deterministic_rows_with_thousands_of_contributions():
     gen = torch.Generator().manual_seed(1600)
     for maps, A in (([[(2, 2), (1, 1)]] * 2, 200), ([[(2, 2), (1, 1)]] * 2, 60), ([[(4, 4), (2, 3)]] * 3, 12)):
         pr = inputs.make_problem(gen, B=1, cam_maps=maps, C=32, G=4, A=A, P=8, loc_range=(0.0, 1.0))
-        a = gpu_backward(pr, True, 8)
-        b = gpu_backward(pr, True, 2)
-        for x, y in zip(a, b):
-            assert torch.equal(x, y)
-        check_against_oracle(pr, a, TOL_FP32, f"many contributions per row A={A}")
+        for variant in (0, 5):  # the cell-binned form and the corner-slot form with its per-row sorts
+            a = gpu_backward(pr, True, 8, variant)
+            b = gpu_backward(pr, True, 2, variant)
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+            check_against_oracle(pr, a, TOL_FP32, f"many contributions per row A={A} variant={variant}")
