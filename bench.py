@@ -3,8 +3,9 @@
 
 One step = one training pass of the operator over one frame of the
 outside-in 64-camera workload: msda_forward (BF16 features and weights, FP32
-accumulation and output) followed by msda_backward (atomic mode: FP32
-gradients for the features, locations and weights).  Shapes: B=1, 64 cameras,
+accumulation and output) followed by msda_backward (deterministic mode, or
+the atomic one with --atomic: FP32 gradients for the features, locations and
+weights).  Shapes: B=1, 64 cameras,
 maps 68x120, 34x60, 17x30, 9x15 (1080p at strides 8..64), C=256, G=8,
 A=900 anchors, P=13 keypoints, 40% of (anchor, camera) pairs out of view.
 Inputs are synthetic and seeded (paper_2601_10819_gb300.inputs, workload 2).
@@ -12,12 +13,14 @@ Inputs are synthetic and seeded (paper_2601_10819_gb300.inputs, workload 2).
 Printed: one JSON line with the metric (us/frame, lower is better), the
 Gsamples/s throughput, a roofline entry for the dominant kernel, the
 end-to-end number through the public API with host buffers, the FP64 CPU
-oracle timed on a bounded sample, and the SM clocks seen during the timed
-region.
+oracle timed on a bounded sample, the SM clocks seen during the timed
+region, and (N = 1) the other forms of the path timed in the same run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank processes its own frame (weak scaling,
-no collective on the data path); the step time is the max over ranks.
+no collective on the data path); the step time is the max over ranks.  With
+--split cameras the ranks share one frame by camera instead (strong
+scaling, one NCCL sum all-reduce of the partial output per step).
 """
 from __future__ import annotations
 
@@ -41,23 +44,22 @@ import torch  # noqa: E402
 METRIC = "MSDA fwd+bwd µs/frame @64 cams bf16; Gsamples/s; % gather roofline"
 UNIT = "µs/frame"
 WORKLOAD = ("outside-in-64cam fwd+bwd: B1 Ncam64 maps 68x120/34x60/17x30/9x15 C256 G8 A900 P13, "
-            "40% of (anchor,camera) pairs out of view, BF16 feat+weights, FP32 accumulate/out/grads, "
-            "atomic backward")
+            "40% of (anchor,camera) pairs out of view, BF16 feat+weights, FP32 accumulate/out/grads")
 # Other workloads the step can run on (diagnostics and profiles; the benchmark line is the default one):
 # name -> (workload index, feature dtype, weight dtype, description)
 WORKLOADS = {
     "outside-in-64cam": (2, None, None, WORKLOAD),
     "train-16cam": (3, None, None, "train-16cam fwd+bwd: B4 Ncam16 maps 64x176/32x88/16x44/8x22 C256 G8 A900 P13, "
-                                   "BF16 feat, FP32 weights/accumulate/out/grads, atomic backward"),
+                                   "BF16 feat, FP32 weights/accumulate/out/grads"),
     "sparse4d-6cam-bf16": (1, "bf16", "bf16", "sparse4d-6cam fwd+bwd: B1 Ncam6 maps 64x176/32x88/16x44/8x22 C256 G8 "
-                                              "A900 P13, BF16 feat+weights, FP32 accumulate, atomic backward"),
+                                              "A900 P13, BF16 feat+weights, FP32 accumulate"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
@@ -67,7 +69,13 @@ def parse():
     ap.add_argument("--copy-streams", type=int, default=1, help="streams per copy direction in the end-to-end run")
     ap.add_argument("--cpu-sample-anchors", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--deterministic", action="store_true", help="time the deterministic backward instead")
+    ap.add_argument("--atomic", action="store_true",
+                    help="time the atomic backward (FP32 vector reductions) instead of the deterministic one")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="the deterministic backward (the default; kept for older command lines)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other timed forms (6-camera forwards, standalone forward, the other backward "
+                         "mode, batched serving)")
     ap.add_argument("--clear", default="forward", choices=["forward", "side", "inline"],
                     help="atomic backward: clear the feature gradient inside the forward kernel "
                          "(msda_forward_train), on a side stream during the forward (side), or with a memset "
@@ -81,7 +89,11 @@ def parse():
                     help="also time the 6-camera (FP32, BF16) and 16-camera training workloads")
     ap.add_argument("--with-batched", action="store_true",
                     help="also time the 16-scene batched serving workload (per-scene p50/p99)")
-    return ap.parse_args()
+    ap.add_argument("--split", default="replicas", choices=["replicas", "cameras"],
+                    help="N > 1: every rank runs its own frame (replicas, weak scaling) or the ranks split one "
+                         "frame's cameras and sum the partial outputs with one NCCL all-reduce (cameras, strong "
+                         "scaling)")
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -98,6 +110,30 @@ def max_over_ranks(values, device):
             torch.distributed.get_world_size() > 1:
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return t.tolist()
+
+
+def split_shard(tensors, rank, world):
+    """Camera split: this rank's cameras and its shard of the frame (maps re-packed, location and weight
+    slices of its cameras)."""
+    from paper_2601_10819_gb300 import shard
+    cams = shard.split_cameras(tensors[1].shape[0], world)[rank]
+    return cams, shard.shard_problem(*tensors, cams)
+
+
+def split_step(sub, grad_out, forward, backward, group=None):
+    """One step of the camera split on this rank: the shard's partial output, completed by one sum all-reduce
+    over the ranks (the frame's output on every rank), then the shard's gradients for the full grad_out."""
+    from paper_2601_10819_gb300 import shard
+    out = forward(*sub)
+    shard.reduce_partials(out, group)
+    return out, backward(*sub, grad_out)
+
+
+def backward_launches(det, zeroed=False):
+    """Kernels msda_backward enqueues on the benchmark frame: atomic: the scatter kernel (and a memset unless
+    the forward cleared grad_feat); deterministic: dloc/dw, the cell-binned plan, binning and reduce, and the ten
+    corner-slot launches that find the cell-binned flag set and return at once."""
+    return 14 if det else (1 if zeroed else 2)
 
 
 def peaks():
@@ -360,6 +396,69 @@ def extras(pr, dev, ft, reps=20):
     }
 
 
+def other_forms(dev, stream, pr, cnt, det_step, l2_gbs, l2_red_gbs, hbm_peak, tune_it=True, reps=20):
+    """The other forms of the path timed in the same run as the step, each with its gather-roof fraction:
+    the 6-camera Sparse4D forward in FP32 and BF16, the benchmark frame's standalone forward (no gradient
+    clearing), the backward mode the step does not use, and the 16-scene batched serving launch."""
+    from paper_2601_10819_gb300 import inputs, msda, roofline, tune
+
+    def tm(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps * 1e3
+
+    def fwd_roof(c):
+        return max(c.fwd_hbm_bytes / (hbm_peak * 1e9), c.fwd_l2_gather_bytes / (l2_gbs * 1e9)) * 1e6
+
+    res = {}
+    for name, fdt in (("sparse4d-6cam fwd fp32", "f32"), ("sparse4d-6cam fwd bf16", "bf16")):
+        p1 = inputs.make_workload(1, feat_dtype=fdt, w_dtype=fdt, with_grad=False)
+        c1 = roofline.count(p1)
+        d = p1.to(dev)
+        T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+        out = torch.empty(d.weights.shape[0], d.weights.shape[1], d.feat.shape[2], device=dev)
+        ft = tune.tune_forward(T, out) if tune_it else dict(vec=0, warps=0, workspace=False)
+        us = tm(lambda: msda.forward(*T, out=out, warps=ft["warps"] or None, vec=ft["vec"]))
+        res[name] = {"us_per_frame": us, "gsamples_per_s": c1.nominal_samples / (us * 1e-6) / 1e9,
+                     "gather_roof_us": fwd_roof(c1), "gather_roof_frac": fwd_roof(c1) / us, "tuning": ft}
+        del d, out
+    d = pr.to(dev)
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    B, sum_hw, C = d.feat.shape
+    out = torch.empty(d.grad_out.shape, device=dev)
+    ft = tune.tune_forward(T, out) if tune_it else dict(vec=0, warps=0, workspace=False)
+    us = tm(lambda: msda.forward(*T, out=out, warps=ft["warps"] or None, vec=ft["vec"]))
+    res["outside-in-64cam fwd standalone"] = {
+        "us_per_frame": us / B, "gsamples_per_s": cnt.nominal_samples / (us * 1e-6) / 1e9,
+        "gather_roof_us": fwd_roof(cnt), "gather_roof_frac": fwd_roof(cnt) / us}
+    det = not det_step
+    grads = (torch.empty(B, sum_hw, C, device=dev), torch.empty(d.sampling_location.shape, device=dev),
+             torch.empty(d.weights.shape, device=dev))
+    K, S = d.weights.shape[3], d.weights.shape[4]
+    A, P, G = d.weights.shape[1], d.weights.shape[2], d.weights.shape[5]
+    ws = torch.empty(max(16, msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, det)), dtype=torch.uint8,
+                     device=dev)
+    us = tm(lambda: msda.backward(*T, d.grad_out, deterministic=det, workspace=ws, grads=grads))
+    red = cnt.bwd_l2_bytes - cnt.fwd_l2_gather_bytes
+    t_hbm = cnt.bwd_hbm_bytes / (hbm_peak * 1e9) * 1e6
+    if det:  # gathers: corner rows and, per in-bound corner, its anchor's grad_out row (no L2 reductions)
+        roof = max(t_hbm, (cnt.fwd_l2_gather_bytes + red) / (l2_gbs * 1e9) * 1e6)
+    else:
+        roof = max(t_hbm, cnt.fwd_l2_gather_bytes / (l2_gbs * 1e9) * 1e6, red / (l2_red_gbs * 1e9) * 1e6)
+    res["outside-in-64cam bwd " + ("deterministic" if det else "atomic (with its clearing of grad_feat)")] = {
+        "us_per_frame": us / B, "roof_us": roof, "roof_frac": roof / us}
+    del d, out, grads, ws
+    res["batched-serving fwd"] = batched_serving(dev, stream, tune_it=tune_it, reps=reps)
+    return res
+
+
 def other_configs(dev, l2_gbs, l2_red_gbs, hbm_peak, reps=20):
     """Forward and atomic backward timings of the non-headline workloads, each with its roofline: the
     forward against max(HBM, L2 gathers), the backward against max(HBM, L2 gathers, L2 FP32 reductions).
@@ -408,6 +507,105 @@ def other_configs(dev, l2_gbs, l2_red_gbs, hbm_peak, reps=20):
     return res
 
 
+def run_camera_split(args, rank, world, local):
+    """--split cameras: the ranks share one frame by camera (Sec. 3.2: the operator is a sum over cameras).
+    Rank r holds only its cameras' maps and their location and weight slices; a step is the shard's forward,
+    one NCCL sum all-reduce of the FP32 partial output [B, A, C], and the shard's backward for the full
+    grad_out.  The job processes B frames per step whatever N is (strong scaling)."""
+    from paper_2601_10819_gb300 import build as msda_build
+    from paper_2601_10819_gb300 import inputs, msda, shard, tune
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        msda_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    msda.load()
+    wl_idx, wl_f, wl_w, wl_desc = WORKLOADS[args.workload]
+    pr = inputs.make_workload(wl_idx, **({"feat_dtype": wl_f, "w_dtype": wl_w} if wl_f else {}))
+    cams, sub = split_shard(pr.tensors(), rank, world)
+    sub = tuple(t.to(dev) for t in sub)
+    go = pr.grad_out.to(dev)
+    B, A, C = go.shape
+    det = not args.atomic
+    sum_hw, K, S, P, G = sub[0].shape[1], sub[3].shape[3], sub[4].shape[4], sub[4].shape[2], sub[4].shape[5]
+    out_buf = torch.empty(B, A, C, device=dev)
+    grads = (torch.empty(B, sum_hw, C, device=dev), torch.empty(sub[3].shape, device=dev),
+             torch.empty(sub[4].shape, device=dev))
+    ws = torch.empty(max(16, msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, det)), dtype=torch.uint8,
+                     device=dev)
+    if args.no_tune:
+        ft, bt = dict(vec=0, warps=0), dict(vec=0, warps=0)
+    else:  # the shard's own launch mappings (untimed)
+        ft = tune.tune_forward(sub, out_buf)
+        bt = tune.tune_backward(sub, go, grads, deterministic=det, workspace=ws)
+
+    def fwd(*t):
+        return msda.forward(*t, out=out_buf, warps=ft["warps"] or None, vec=ft["vec"])
+
+    def bwd(*t):
+        return msda.backward(*t, deterministic=det, workspace=ws, grads=grads, warps=bt["warps"] or None,
+                             vec=bt["vec"])
+
+    for _ in range(args.warmup):
+        split_step(sub, go, fwd, bwd)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            e = evs[i]
+            e[0].record(stream)
+            out = fwd(*sub)
+            e[1].record(stream)
+            shard.reduce_partials(out)
+            e[2].record(stream)
+            bwd(*sub, go)
+            e[3].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = start.elapsed_time(end)
+    fwd_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    ar_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    bwd_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
+    total_ms, fwd_ms, ar_ms, bwd_ms = max_over_ranks([total_ms, fwd_ms, ar_ms, bwd_ms], dev)
+    if msda.device_status() != 0:
+        raise RuntimeError("device status set during the timed region")
+    per_rank = [len(c) for c in shard.split_cameras(pr.spatial_shape.shape[0], world)]
+    ms_per_step = total_ms / args.steps
+    line = {
+        "metric": METRIC, "value": ms_per_step * 1e3 / B, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "strong",
+        "vs_baseline": None, "dtype": "bf16", "accumulate": "f32", "data": "synthetic",
+        "config": {"workload": wl_desc, "frames_per_step": B,
+                   "parallelism": f"camera split x{world}: rank r owns cameras split_cameras(Ncam, {world})[r] "
+                                  f"with their maps; one NCCL sum all-reduce of out [B, A, C] FP32 per step",
+                   "cameras_per_rank": per_rank, "backward": "deterministic" if det else "atomic",
+                   "l2": "inputs larger than L2 on one GPU; no flush"},
+        "fwd_us": fwd_ms * 1e3, "allreduce_us": ar_ms * 1e3, "bwd_us": bwd_ms * 1e3,
+        "allreduce_bytes_per_step": B * A * C * 4 if world > 1 else 0,
+        "e2e": None,  # the end-to-end number is measured by the default (replica) mode
+        "gpu_launches": (1 + backward_launches(det)) * args.steps,
+        "clocks": clk.summary(),
+        "gpu": torch.cuda.get_device_name(dev),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle, timed on the host cores."""
     if rank != 0:
@@ -425,7 +623,7 @@ def run_reference(args, rank, world):
     budget_s = 120.0
     per_anchor_s = 0.02
     na = int(max(1, min(A, budget_s / max(1, args.steps + args.warmup) / per_anchor_s)))
-    times = []
+    times, raw = [], []
     for it in range(args.warmup + args.steps):
         a0 = (it * na) % A
         idx = [(a0 + j) % A for j in range(na)]
@@ -437,13 +635,19 @@ def run_reference(args, rank, world):
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt * A / na)
+            raw.append(dt)
     v = statistics.mean(times) * 1e6
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v / 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl_desc, "parallelism": "host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                             "sample": f"{na} anchors of {A} per step, scaled to a frame"},
+                             "sample": f"{na} anchors of {A} per step (forward on {nthreads} threads, backward "
+                                       f"single-threaded), scaled to a frame by {A}/{na}"},
+            # value and ms_per_step are a frame's time extrapolated from the anchor sample, not the wall time of
+            # a step; measured_ms_per_step is the sample's own time
+            "extrapolated": True, "frame_scale": A / na,
+            "measured_ms_per_step": statistics.mean(raw) * 1e3,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -457,6 +661,8 @@ def main():
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.split == "cameras":
+        return run_camera_split(args, rank, world, local)
 
     from paper_2601_10819_gb300 import build as msda_build
     from paper_2601_10819_gb300 import inputs, msda, roofline, tune
@@ -482,7 +688,7 @@ def main():
     gf = torch.empty(B, sum_hw, C, device=dev)
     gl = torch.empty(B, A, P, K, 2, device=dev)
     gw = torch.empty(B, A, P, K, S, G, device=dev)
-    det = bool(args.deterministic)
+    det = not args.atomic
     ws = None
     need = msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, det)
     if need:
@@ -712,12 +918,16 @@ def main():
                             f"direction's copies cut over {nsplit} streams)",
                 "copy_floor": {"value": copy_ms * 1e3 / B, "unit": UNIT, "frac": copy_ms / e2e_ms,
                                "what": "the step's host<->device copies alone, both directions at once"}},
-        "gpu_launches": ((2 if fwd_ws is not None and not fwd_clear else 1) + (1 if not det else 10)) * args.steps,
+        "gpu_launches": ((2 if fwd_ws is not None and not fwd_clear else 1) + backward_launches(det, fwd_clear))
+                        * args.steps,
         "tuning": {"forward": ft, "backward": bt},
         "clocks": clk.summary(),
         "gpu": torch.cuda.get_device_name(dev),
     }
-    if args.with_batched:
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["forms"] = other_forms(dev, stream, pr, cnt, det, l2_gather_gbs, l2_red_gbs, hbm_peak,
+                                    tune_it=not args.no_tune)
+    if args.with_batched and "forms" not in line:
         line["batched_serving"] = batched_serving(dev, stream, tune_it=not args.no_tune)
     if args.extras:
         line["extras"] = extras(pr, dev, ft)

@@ -327,6 +327,20 @@ msda_status msda_forward_batched_noalloc(const msda_scene* scenes, int num_scene
 /* ------------------------------------------------------------------------
  * Status and diagnostics
  * ------------------------------------------------------------------------ */
+/* Testing aid (no counterpart in the paper): the staged kernels (the
+ * staged forward with a workspace, the staged and the cell-binned
+ * deterministic backward) wait on an mbarrier for each set of bulk copies
+ * they issue, polling at most a fixed number of times (about 2^26, seconds)
+ * before they give up, set MSDA_ERR_TIMEOUT in the device status word and
+ * skip the work that needed the copies.  This sets the poll limit of that
+ * first wait on the current device: polls > 0 polls that many times,
+ * polls = 0 gives up at once (so the next staged call reports
+ * MSDA_ERR_TIMEOUT and computes wrong results), polls < 0 restores the
+ * default.  After a give-up a second wait with the full limit lets the copies
+ * in flight land before the block moves on.  Synchronous (a copy to a
+ * device variable); not for use during stream capture. */
+msda_status msda_debug_set_wait_limit(long long polls);
+
 /* Synchronises `stream`, returns the device status word of the current
  * device (MSDA_OK if no kernel reported a problem since the last read) and
  * clears it. */

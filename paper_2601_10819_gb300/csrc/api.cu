@@ -376,6 +376,15 @@ msda_status msda_keypoints(const float* anchors, const float* offsets, const flo
                             (cudaStream_t)stream);
 }
 
+msda_status msda_debug_set_wait_limit(long long polls) {
+    t_err[0] = 0;
+    DeviceInfo dev;
+    msda_status st = device_info(&dev);
+    if (st != MSDA_OK) return st;
+    if ((st = cg_set_wait_limit(polls)) != MSDA_OK) return st;
+    return cb_set_wait_limit(polls);
+}
+
 msda_status msda_get_device_status(msda_stream_t stream) {
     DeviceInfo dev;
     msda_status st = device_info(&dev);

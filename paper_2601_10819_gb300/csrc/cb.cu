@@ -687,17 +687,10 @@ __global__ void __launch_bounds__(kCbThreads, 1) cb_reduce_kernel(const CbArgs a
                 for (int k = 0; k < nb; ++k) {
                     const int bf = k & 1;
                     const uint32_t par = bf ? ph1 : ph0;
-                    if (threadIdx.x == 0) {
-                        long long spins = 0;
-                        while (!mbar_try_wait(&mbar[bf], par)) {
-                            if (++spins > kSpinLimit) {
-                                s_fail = 1;
-                                raise_status(a.status, MSDA_ERR_TIMEOUT);
-                                spins = 0;  // one more bounded wait for the copies in flight
-                                while (!mbar_try_wait(&mbar[bf], par) && ++spins < kSpinLimit) {}
-                                break;
-                            }
-                        }
+                    if (threadIdx.x == 0 && !mbar_wait_first(&mbar[bf], par)) {
+                        s_fail = 1;
+                        raise_status(a.status, MSDA_ERR_TIMEOUT);
+                        mbar_wait_drain(&mbar[bf], par);  // the copies in flight land before the buffer is reused
                     }
                     __syncthreads();
                     if (bf) ph1 ^= 1u; else ph0 ^= 1u;
@@ -804,6 +797,13 @@ msda_status launch_backward_cb(const Problem& p, const float* grad_out, float* g
     const int ngb = dev.sm_count / p.G;
     red<<<(unsigned)(ngb * p.G), kCbThreads, red_smem, stream>>>(a);
     return check_launch("msda_backward cell-binned");
+}
+
+// The first-wait poll limit of this file's band waits (msda_debug_set_wait_limit).
+msda_status cb_set_wait_limit(long long polls) {
+    if (polls < 0) polls = kSpinLimit;
+    const cudaError_t e = cudaMemcpyToSymbol(g_first_wait_limit, &polls, sizeof(polls));
+    return e == cudaSuccess ? MSDA_OK : fail(MSDA_ERR_CUDA, "msda_debug_set_wait_limit: %s", cudaGetErrorString(e));
 }
 
 }  // namespace msda

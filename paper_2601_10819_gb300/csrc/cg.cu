@@ -137,15 +137,10 @@ __device__ bool stage_unit(const CUtensorMap* tmap, const CgArgs& p, const UnitI
             for (int i = 0; i < nbox; ++i)
                 tma_load_2d(stage + (size_t)(soff[s] + i * kCgBoxRows) * rowbytes, tmap, x, y0 + i * kCgBoxRows, bar);
         }
-        long long spins = 0;
-        bool ok = true;
-        while (!mbar_try_wait(bar, phase)) {
-            if (++spins > kSpinLimit) { ok = false; break; }
-        }
+        const bool ok = mbar_wait_first(bar, phase);
         if (!ok) {
             raise_status(p.status, MSDA_ERR_TIMEOUT);
-            spins = 0;  // give the copies in flight one more bounded chance before the CTA leaves
-            while (!mbar_try_wait(bar, phase) && ++spins < kSpinLimit) {}
+            mbar_wait_drain(bar, phase);  // the copies in flight land before the CTA goes on
         }
         *sflag = ok ? 1 : 0;
     }
@@ -1003,6 +998,13 @@ msda_status launch_backward_cg(const Problem& p, const float* grad_out, float* g
     if (grid > (long long)dev.sm_count * 64) grid = (long long)dev.sm_count * 64;
     row_gather_kernel<<<(unsigned)grid, 512, gsmem, stream>>>(ra);
     return check_launch("msda_backward row gather");
+}
+
+// The first-wait poll limit of this file's staged kernels (msda_debug_set_wait_limit).
+msda_status cg_set_wait_limit(long long polls) {
+    if (polls < 0) polls = kSpinLimit;
+    const cudaError_t e = cudaMemcpyToSymbol(g_first_wait_limit, &polls, sizeof(polls));
+    return e == cudaSuccess ? MSDA_OK : fail(MSDA_ERR_CUDA, "msda_debug_set_wait_limit: %s", cudaGetErrorString(e));
 }
 
 }  // namespace msda

@@ -80,6 +80,10 @@ size_t cb_plan_bytes(const Problem& p);
 size_t cb_workspace(const Problem& p, size_t body_base);
 msda_status launch_backward_cb(const Problem& p, const float* grad_out, float* grad_feat, void* ws,
                                size_t body_base, cudaStream_t stream);
+// Poll limit of the first wait of each staging step of the staged kernels (cg.cu, cb.cu); see
+// msda_debug_set_wait_limit.
+msda_status cg_set_wait_limit(long long polls);
+msda_status cb_set_wait_limit(long long polls);
 size_t batched_workspace(int num_scenes);
 msda_status launch_forward_batched(const msda_scene* scenes, int num_scenes, int total_anchors,
                                    int max_ncam, int Nscale, int C, int P, int G, msda_dtype ft,

@@ -7,6 +7,11 @@ namespace msda {
 
 constexpr long long kSpinLimit = 1ll << 26;  // bounded mbarrier wait (~seconds)
 
+// Poll limit of the first wait of a staging step in the translation unit that includes this header: kSpinLimit
+// unless msda_debug_set_wait_limit lowered it (0: give up at once).  The wait that drains the copies after a
+// give-up always keeps kSpinLimit, so no copy is in flight when a block leaves.
+static __device__ long long g_first_wait_limit = kSpinLimit;
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -29,6 +34,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// First wait of a staging step: true when the phase completed within the limit.
+__device__ __forceinline__ bool mbar_wait_first(uint64_t* bar, uint32_t parity) {
+    const long long lim = g_first_wait_limit;
+    if (lim <= 0) return false;
+    long long spins = 0;
+    while (!mbar_try_wait(bar, parity))
+        if (++spins > lim) return false;
+    return true;
+}
+
+// Drain wait after a first wait gave up: the full limit, so the copies in flight land before the block goes on.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+    long long spins = 0;
+    while (!mbar_try_wait(bar, parity))
+        if (++spins > kSpinLimit) return false;
+    return true;
 }
 
 // 1D bulk copy global -> shared (both addresses 16-byte aligned, bytes a multiple of 16), completing on `bar`.

@@ -98,6 +98,8 @@ def load(path: Optional[str] = None):
         lib.msda_probe_read.restype = i
         lib.msda_probe_reduce.argtypes = [vp, sz, i, i, i, vp]
         lib.msda_probe_reduce.restype = i
+        lib.msda_debug_set_wait_limit.argtypes = [ctypes.c_longlong]
+        lib.msda_debug_set_wait_limit.restype = i
         if path is None:
             _lib = lib
         return lib
@@ -292,6 +294,12 @@ def backward(feat, spatial_shape, scale_start_index, sampling_location, weights,
                            ctypes.c_void_p(_stream(dev)))
     _check("msda_backward", rc)
     return gf, gl, gw
+
+
+def debug_set_wait_limit(polls: int):
+    """msda_debug_set_wait_limit: poll limit of the staged kernels' first wait (0: give up at once; < 0:
+    the default).  A testing aid."""
+    _check("msda_debug_set_wait_limit", load().msda_debug_set_wait_limit(int(polls)))
 
 
 def device_status(stream=None) -> int:

@@ -113,21 +113,29 @@ def test_outside_in_64cam_full_backward():
             assert e <= TOL_LOWP_GRAD
 
 
-def test_train_16cam_full_adjoint_and_sampled_anchors():
-    """Full size B=4 x 16 cameras: adjoint identities plus exact per-anchor checks on sampled anchors."""
+def test_train_16cam_full_elementwise():
+    """The 16-camera training batch at full size (B=4, BF16 features, FP32 weights): every element of the three
+    gradients against the oracle, frame by frame, in the atomic and the deterministic mode; plus the adjoint
+    identities <grad_out, out> = <grad_feat, feat> = <grad_w, w> on the whole batch."""
     pr = inputs.make_workload(3)
     d = pr.to("cuda")
-    out = msda.forward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
-    gf, gl, gw = msda.backward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights,
-                               d.grad_out)
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    out = msda.forward(*T)
+    modes = {det: [g.cpu() for g in msda.backward(*T, d.grad_out, deterministic=det)] for det in (False, True)}
+    gf = modes[False][0]
     lhs = float((d.grad_out.double() * out.double()).sum())
-    assert abs(lhs - float((gf.double() * d.feat.double()).sum())) <= 1e-4 * abs(lhs)
-    assert abs(lhs - float((gw.double() * d.weights.double()).sum())) <= 1e-4 * abs(lhs)
-    idx = torch.randperm(900, generator=torch.Generator().manual_seed(0))[:24]
-    sub = pr.anchors(idx)
-    _, rl, rw = oracle_backward(sub)
-    assert relerr(gl.cpu()[:, idx].double().numpy(), rl) <= TOL_LOWP_GRAD
-    assert relerr(gw.cpu()[:, idx].double().numpy(), rw) <= TOL_LOWP_GRAD
+    assert abs(lhs - float((gf.double() * pr.feat.double()).sum())) <= 1e-4 * abs(lhs)
+    assert abs(lhs - float((modes[False][2].double() * pr.weights.double()).sum())) <= 1e-4 * abs(lhs)
+    for b in range(pr.feat.shape[0]):
+        frame = inputs.Problem(pr.feat[b:b + 1].contiguous(), pr.spatial_shape, pr.scale_start_index,
+                               pr.sampling_location[b:b + 1].contiguous(), pr.weights[b:b + 1].contiguous(),
+                               pr.grad_out[b:b + 1].contiguous())
+        ref = oracle_backward(frame)
+        for det, grads in modes.items():
+            for name, g, r in zip(("dfeat", "dloc", "dw"), grads, ref):
+                e = relerr(g[b:b + 1].double().numpy(), r)
+                print(f"train-16cam frame {b} det={det} {name} rel err {e:.2e}")
+                assert e <= TOL_LOWP_GRAD, (b, det, name, e)
 
 
 def test_autograd_function_matches_direct_calls_and_gradcheck():

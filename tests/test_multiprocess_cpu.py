@@ -87,6 +87,54 @@ def test_split_cameras_covers_each_camera_once():
             assert max(len(p) for p in parts) - min(len(p) for p in parts) <= 1
 
 
+def _bench_split(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        import oracle
+        oracle.build()
+        gen = torch.Generator().manual_seed(8)
+        maps = [[(9, 11), (5, 6)], [(7, 7), (4, 4)], [(12, 5), (6, 3)], [(6, 10), (3, 5)], [(8, 8), (4, 4)]]
+        pr = inputs.make_problem(gen, B=2, cam_maps=maps, C=16, G=4, A=9, P=3, loc_range=(-0.2, 1.2))
+        cams, sub = bench.split_shard(pr.tensors(), rank, world)
+        fwd = lambda *t: torch.from_numpy(oracle.forward(*t))  # noqa: E731  the kernels' stand-in on a CPU
+        bwd = lambda *t: oracle.backward(*t)  # noqa: E731
+        out, (gf, gl, gw) = bench.split_step(sub, pr.grad_out, fwd, bwd)
+        full = oracle.forward(*pr.tensors())
+        fgf, fgl, fgw = oracle.backward(*pr.tensors(), pr.grad_out)
+        q.put((f"out{rank}", float(np.abs(out.numpy() - full).max() / np.abs(full).max())))
+        q.put((f"cams{rank}", cams))
+        q.put((f"dloc{rank}", float(np.abs(gl - fgl[:, :, :, cams]).max())))
+        q.put((f"dw{rank}", float(np.abs(gw - fgw[:, :, :, cams]).max())))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_camera_split_step():
+    """bench.py --split cameras: every rank ends the forward with the frame's output (its shard's partial
+    output plus the other rank's, one sum all-reduce) and holds its cameras' gradients."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_split, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(240)
+        assert p.exitcode == 0
+    res = {}
+    while not q.empty():
+        k, v = q.get()
+        res[k] = v
+    assert sorted(res["cams0"] + res["cams1"]) == list(range(5))
+    for r in range(2):
+        assert res[f"out{r}"] <= 1e-13
+        assert res[f"dloc{r}"] <= 1e-13 and res[f"dw{r}"] <= 1e-13
+
+
 def _timing(rank, world, port, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
