@@ -53,7 +53,8 @@ struct CbHeader {
 
 struct CbLayout {
     size_t maps, gaps, queues, plan_end;  // plan area (read by the corner-slot kernels: header.ok)
-    size_t cellptr, aoff, coef, total;    // cell pointers, anchor offsets, per-group corner coefficients
+    size_t cellptr, aoff, coef, loct;     // cell pointers, anchor offsets, per-group corner coefficients,
+    size_t total;                         // locations camera-major [B, Ncam, A*P] (float2)
     long long nccap;                      // cell-pointer entries per batch element
     long long nrec;                       // record slots: B * Nmaps * A * P
 };
@@ -73,7 +74,8 @@ static CbLayout cb_layout(const Problem& p, size_t body_base = 0) {
     // 16 spare bytes after the cell pointers and the anchor offsets: band copies round their ends up to 16 bytes
     L.aoff = align_up(L.cellptr + sizeof(uint32_t) * (size_t)p.B * L.nccap + 16, 256);
     L.coef = align_up(L.aoff + sizeof(uint32_t) * (size_t)L.nrec + 16, 256);
-    L.total = align_up(L.coef + sizeof(float4) * (size_t)p.G * L.nrec, 256);
+    L.loct = align_up(L.coef + sizeof(float4) * (size_t)p.G * L.nrec, 256);
+    L.total = align_up(L.loct + sizeof(float2) * (size_t)p.B * p.Ncam * p.A * p.P, 256);
     return L;
 }
 
@@ -235,8 +237,11 @@ __global__ void __launch_bounds__(kCbThreads) cb_plan_kernel(const CbArgs a) {
         key[m] = kv;
     }
     __syncthreads();
-    // valid maps in order of their first row (bitonic sort; invalid maps sort last)
-    for (int k = 2; k <= np2; k <<= 1) {
+    // valid maps in order of their first row (bitonic sort; invalid maps sort last), unless they already are
+    int unsorted = 0;
+    for (int m = threadIdx.x; m + 1 < np2; m += blockDim.x) unsorted |= key[m] > key[m + 1];
+    unsorted = __syncthreads_or(unsorted);
+    for (int k = 2; unsorted && k <= np2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < np2; i += blockDim.x) {
                 const int ij = i ^ j;
@@ -251,10 +256,12 @@ __global__ void __launch_bounds__(kCbThreads) cb_plan_kernel(const CbArgs a) {
             __syncthreads();
         }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) s_nvalid = 0;
+    __syncthreads();
+    {
         int n = 0;
-        while (n < nm && key[n] != ~0ull) ++n;  // valid keys come first
-        s_nvalid = n;
+        for (int m = threadIdx.x; m < nm; m += blockDim.x) n += key[m] != ~0ull;  // valid keys come first
+        if (n) atomicAdd(&s_nvalid, n);
     }
     __syncthreads();
     const int nv = s_nvalid;
@@ -340,17 +347,17 @@ __global__ void __launch_bounds__(kCbThreads, 2) cb_bin_kernel(const CbArgs a) {
     const CbMap* maps = reinterpret_cast<const CbMap*>(a.ws + a.L.maps);
     const long long nbm = (long long)a.B * a.nmaps;
     if ((long long)blockIdx.x >= nbm) {
-        // rows of no valid map: zero gradient
+        // rows of no valid map: zero gradient; the extra blocks take the uncovered ranges in turn
         const int2* gaps = reinterpret_cast<const int2*>(a.ws + a.L.gaps);
-        const long long zb = blockIdx.x - nbm, nzb = gridDim.x - nbm;
+        const int zb = (int)(blockIdx.x - nbm), nzb = (int)(gridDim.x - nbm);
         const int c4 = a.C / 4;
-        for (int gi = 0; gi < hdr->ngaps; ++gi) {
+        const int ngaps = hdr->ngaps;
+        for (int gi = zb; gi < ngaps; gi += nzb) {
             const int2 gp = gaps[gi];
             const long long n = (long long)(gp.y - gp.x) * c4;
-            for (int b = 0; b < a.B; ++b) {
+            for (int b = 0; b < a.B && n > 0; ++b) {
                 float4* dst = reinterpret_cast<float4*>(a.gfeat + ((long long)b * a.sum_hw + gp.x) * a.C);
-                for (long long i = zb * blockDim.x + threadIdx.x; i < n; i += nzb * blockDim.x)
-                    dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (long long i = threadIdx.x; i < n; i += blockDim.x) dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         return;
@@ -362,25 +369,33 @@ __global__ void __launch_bounds__(kCbThreads, 2) cb_bin_kernel(const CbArgs a) {
     const int H = mp.H, W = mp.W, W1 = W + 1;
     const int ncell = (H + 1) * W1;
     const int ap = a.A * a.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Maps of few cells place their points stably with per-warp cell cursors (each warp owns a chunk of the
+    // points); maps of many cells with one counter per cell and a sort of every cell afterwards.
+    const size_t arrays = cb_bin_fixed(ap);
+    const bool stable = align16((size_t)kCbWarps * 4 * (ncell + 1)) + arrays <= (size_t)a.bin_smem;
+    const int cstride = ncell + 1;  // stable: counter of (cell c, warp w) at w * cstride + c
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* cnt = reinterpret_cast<uint32_t*>(smem);
-    unsigned short* cell = reinterpret_cast<unsigned short*>(smem + align16(4 * (size_t)(ncell + 1)));
+    const size_t cbytes = align16(4 * (size_t)(stable ? kCbWarps * cstride : ncell + 1));
+    unsigned short* cell = reinterpret_cast<unsigned short*>(smem + cbytes);
     unsigned short* idx = cell + align16(2 * (size_t)ap) / 2;
     uint32_t* lng = reinterpret_cast<uint32_t*>(idx + align16(2 * (size_t)ap) / 2);
     __shared__ int wsum[32];
     __shared__ int s_nlong, s_abort;
+    const int chunk = (ap + kCbWarps - 1) / kCbWarps;  // stable: points of warp w are [w * chunk, ...)
+    const int ncnt = stable ? kCbWarps * cstride : ncell + 1;
 
-    for (int c = threadIdx.x; c <= ncell; c += blockDim.x) cnt[c] = 0u;
+    for (int c = threadIdx.x; c < ncnt; c += blockDim.x) cnt[c] = 0u;
     if (threadIdx.x == 0) { s_nlong = 0; s_abort = 0; }
     __syncthreads();
-    const float2* gloc = reinterpret_cast<const float2*>(a.loc);
-    const long long tbase = ((long long)b * a.A * a.P) * a.Ncam + k;  // point (a, p) is tbase + (a*P + p)*Ncam
+    const float2* lk = reinterpret_cast<const float2*>(a.ws + a.L.loct) + ((long long)b * a.Ncam + k) * ap;
     for (int i0 = threadIdx.x; i0 < ap; i0 += 4 * blockDim.x) {
         float2 uv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int i = i0 + u * blockDim.x;
-            uv[u] = i < ap ? __ldg(gloc + tbase + (long long)i * a.Ncam) : make_float2(-9.f, -9.f);
+            uv[u] = i < ap ? __ldg(lk + i) : make_float2(-9.f, -9.f);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -390,22 +405,28 @@ __global__ void __launch_bounds__(kCbThreads, 2) cb_bin_kernel(const CbArgs a) {
                 unsigned short c = kNoCell;
                 if (locate(uv[u].x, uv[u].y, H, W, cl)) {
                     c = (unsigned short)((cl.y0 + 1) * W1 + cl.x0 + 1);
-                    atomicAdd(cnt + c, 1u);
+                    atomicAdd(cnt + (stable ? (i / chunk) * cstride + c : c), 1u);
                 }
                 cell[i] = c;
             }
         }
     }
     __syncthreads();
-    // exclusive scan of the ncell + 1 counters (the last one is 0, so it receives the total); cell pointers
+    // exclusive scan of the counters in (cell, warp) order (the end entry is 0, so it receives the total);
+    // the start of cell c, its first warp's entry, is its cell pointer
     const uint32_t recbase = (uint32_t)(((long long)b * a.nmaps + m) * ap);
     {
         uint32_t* gptr = reinterpret_cast<uint32_t*>(a.ws + a.L.cellptr) + (long long)b * a.L.nccap + mp.cbase;
-        const int per = (ncell + 1 + blockDim.x - 1) / blockDim.x;
+        const int nw = stable ? kCbWarps : 1;
+        const int nent = stable ? kCbWarps * cstride - (kCbWarps - 1) : ncell + 1;  // (ncell, 0) ends the order
+        const int per = (nent + blockDim.x - 1) / blockDim.x;
         const int c0 = threadIdx.x * per;
+        // scan position q is (cell q / nw, warp q % nw), at counter (q % nw) * cstride + q / nw
         uint32_t sum = 0u;
-        for (int j = 0; j < per && c0 + j <= ncell; ++j) sum += cnt[c0 + j];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int j = 0; j < per && c0 + j < nent; ++j) {
+            const int q = c0 + j;
+            sum += cnt[(q % nw) * cstride + q / nw];
+        }
         uint32_t x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -425,34 +446,67 @@ __global__ void __launch_bounds__(kCbThreads, 2) cb_bin_kernel(const CbArgs a) {
         }
         __syncthreads();
         uint32_t run = x - sum + (warp > 0 ? (uint32_t)wsum[warp - 1] : 0u);
-        for (int j = 0; j < per && c0 + j <= ncell; ++j) {
-            const uint32_t v = cnt[c0 + j];
-            cnt[c0 + j] = run;
-            gptr[c0 + j] = recbase + run;
+        for (int j = 0; j < per && c0 + j < nent; ++j) {
+            const int q = c0 + j;
+            uint32_t* e = cnt + (q % nw) * cstride + q / nw;
+            const uint32_t v = *e;
+            *e = run;
+            if (q % nw == 0) gptr[q / nw] = recbase + run;
             run += v;
         }
     }
     __syncthreads();
-    // place the points; afterwards cnt[c] is the end of cell c
-    for (int i = threadIdx.x; i < ap; i += blockDim.x) {
-        const unsigned short c = cell[i];
-        if (c != kNoCell) idx[atomicAdd(cnt + c, 1u)] = (unsigned short)i;
+    if (stable) {
+        // warp w walks its chunk in point order; ranks inside a batch of 32 from ballots over the cell bits
+        int cbits = 1;
+        while ((1 << cbits) < ncell) ++cbits;
+        const unsigned lt = (1u << lane) - 1u;
+        const int lo = warp * chunk, hi = min(lo + chunk, ap);
+        uint32_t* cur = cnt + warp * cstride;
+        for (int i0 = lo; i0 < hi; i0 += 32) {
+            const int i = i0 + lane;
+            const unsigned c = i < hi ? (unsigned)cell[i] : (unsigned)kNoCell;
+            const bool valid = c != kNoCell;
+            unsigned peers = __ballot_sync(0xffffffffu, valid);
+            for (int bit = 0; bit < cbits; ++bit) {
+                const unsigned mb = __ballot_sync(0xffffffffu, (c >> bit) & 1u);
+                peers &= ((c >> bit) & 1u) ? mb : ~mb;
+            }
+            const int leader = valid ? __ffs(peers) - 1 : 0;
+            uint32_t base = 0u;
+            if (valid && lane == leader) {
+                base = cur[c];
+                cur[c] = base + (uint32_t)__popc(peers);
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (valid) idx[base + __popc(peers & lt)] = (unsigned short)i;
+        }
+    } else {
+        // place the points; afterwards cnt[c] is the end of cell c
+        for (int i = threadIdx.x; i < ap; i += blockDim.x) {
+            const unsigned short c = cell[i];
+            if (c != kNoCell) idx[atomicAdd(cnt + c, 1u)] = (unsigned short)i;
+        }
     }
     __syncthreads();
-    const int total = (int)cnt[ncell];
-    // point order inside every cell
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const int e0 = c > 0 ? (int)cnt[c - 1] : 0, n = (int)cnt[c] - e0;
-        if (n <= 1) continue;
-        if (n <= 4) cb_sort_small<4>(idx + e0, n);
-        else if (n <= 16) cb_sort_small<16>(idx + e0, n);
-        else if (n <= kCbMaxBin) lng[atomicAdd(&s_nlong, 1)] = (uint32_t)c;
-        else s_abort = 1;
+    // end of cell c (the start of cell c + 1): the last warp's cursor when stable, else the counter
+    const uint32_t* cend = stable ? cnt + (kCbWarps - 1) * cstride : cnt;
+    const int total = (int)cend[ncell - 1];
+    if (!stable) {
+        // point order inside every cell
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const int e0 = c > 0 ? (int)cend[c - 1] : 0, n = (int)cend[c] - e0;
+            if (n <= 1) continue;
+            if (n <= 4) cb_sort_small<4>(idx + e0, n);
+            else if (n <= 16) cb_sort_small<16>(idx + e0, n);
+            else if (n <= kCbMaxBin) lng[atomicAdd(&s_nlong, 1)] = (uint32_t)c;
+            else s_abort = 1;
+        }
     }
     // one image row's band (cell rows i-1 and i) must fit a reduce band buffer
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
         const int r0 = i * W1, r2 = (i + 2) * W1;  // first cells of cell rows i - 1 and i + 1
-        const uint32_t s0 = r0 > 0 ? cnt[r0 - 1] : 0u, s2 = cnt[r2 - 1];
+        const uint32_t s0 = r0 > 0 ? cend[r0 - 1] : 0u, s2 = cend[r2 - 1];
         if ((int)(s2 - s0) > a.nb - 8) s_abort = 1;
     }
     __syncthreads();
@@ -460,48 +514,77 @@ __global__ void __launch_bounds__(kCbThreads, 2) cb_bin_kernel(const CbArgs a) {
         if (threadIdx.x == 0) atomicExch(&hdr->ok, 0);
         return;
     }
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int li = warp; li < s_nlong; li += kCbWarps) {
-            const int c = (int)lng[li];
-            const int e0 = c > 0 ? (int)cnt[c - 1] : 0, n = (int)cnt[c] - e0;
-            if (n <= 32) cb_sort_warp<1>(idx + e0, n, lane);
-            else if (n <= 64) cb_sort_warp<2>(idx + e0, n, lane);
-            else if (n <= 128) cb_sort_warp<4>(idx + e0, n, lane);
-            else cb_sort_warp<8>(idx + e0, n, lane);
-        }
+    for (int li = warp; li < s_nlong; li += kCbWarps) {
+        const int c = (int)lng[li];
+        const int e0 = c > 0 ? (int)cend[c - 1] : 0, n = (int)cend[c] - e0;
+        if (n <= 32) cb_sort_warp<1>(idx + e0, n, lane);
+        else if (n <= 64) cb_sort_warp<2>(idx + e0, n, lane);
+        else if (n <= 128) cb_sort_warp<4>(idx + e0, n, lane);
+        else cb_sort_warp<8>(idx + e0, n, lane);
     }
     __syncthreads();
-    // records in record order: anchor offsets and the corner coefficients of each group
+    // records in record order: anchor offsets and the corner coefficients of each group, two at a time
     const long long rb = (long long)recbase;
     uint32_t* aoffp = reinterpret_cast<uint32_t*>(a.ws + a.L.aoff);
     float4* coef = reinterpret_cast<float4*>(a.ws + a.L.coef);
     const WT* wp = reinterpret_cast<const WT*>(a.w);
-    for (int pos = threadIdx.x; pos < total; pos += blockDim.x) {
-        const int i = idx[pos];
-        const int aa = i / a.P;
-        const long long t = tbase + (long long)i * a.Ncam;
-        const float2 uv = __ldg(gloc + t);
-        Cell cl;
-        locate(uv.x, uv.y, H, W, cl);  // in view: it was binned
-        const float ax = 1.0f - cl.fx, ay = 1.0f - cl.fy;
-        const float f00 = ax * ay, f01 = cl.fx * ay, f10 = ax * cl.fy, f11 = cl.fx * cl.fy;
-        aoffp[rb + pos] = (uint32_t)(aa * a.Cg);
-        const WT* wrow = wp + (t * a.Nscale + s) * a.G;
-        for (int g0 = 0; g0 < a.G; g0 += 8) {
-            float v[8];
-            if (a.G - g0 >= 8 && ((size_t)a.G * sizeof(WT)) % 16 == 0) {
-                cb_load8(wrow + g0, v);  // 16-byte aligned: G * sizeof(WT) is a multiple of 16
-            } else {
+    const long long tbase = ((long long)b * a.A * a.P) * a.Ncam + k;  // point (a, p) is tbase + (a*P + p)*Ncam
+    for (int p0 = threadIdx.x; p0 < total; p0 += 2 * blockDim.x) {
+        int ii[2];
+        float2 uv[2];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = g0 + j < a.G ? ldw(wrow + g0 + j) : 0.0f;
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (g0 + j < a.G)
-                    coef[(long long)(g0 + j) * a.L.nrec + rb + pos] =
-                        make_float4(v[j] * f00, v[j] * f01, v[j] * f10, v[j] * f11);
+        for (int u = 0; u < 2; ++u) {
+            const int pos = p0 + u * blockDim.x;
+            ii[u] = pos < total ? (int)idx[pos] : -1;
+            uv[u] = ii[u] >= 0 ? __ldg(lk + ii[u]) : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int pos = p0 + u * blockDim.x;
+            if (ii[u] < 0) continue;
+            const int i = ii[u];
+            Cell cl;
+            locate(uv[u].x, uv[u].y, H, W, cl);  // in view: it was binned
+            const float ax = 1.0f - cl.fx, ay = 1.0f - cl.fy;
+            const float f00 = ax * ay, f01 = cl.fx * ay, f10 = ax * cl.fy, f11 = cl.fx * cl.fy;
+            aoffp[rb + pos] = (uint32_t)((i / a.P) * a.Cg);
+            const WT* wrow = wp + ((tbase + (long long)i * a.Ncam) * a.Nscale + s) * a.G;
+            for (int g0 = 0; g0 < a.G; g0 += 8) {
+                float v[8];
+                if (a.G - g0 >= 8 && ((size_t)a.G * sizeof(WT)) % 16 == 0) {
+                    cb_load8(wrow + g0, v);  // 16-byte aligned: G * sizeof(WT) is a multiple of 16
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = g0 + j < a.G ? ldw(wrow + g0 + j) : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (g0 + j < a.G)
+                        coef[(long long)(g0 + j) * a.L.nrec + rb + pos] =
+                            make_float4(v[j] * f00, v[j] * f01, v[j] * f10, v[j] * f11);
+            }
+        }
+    }
+}
+
+// Locations camera-major: loct[b, k, i] = loc[b, i, k] with i = a * P + p (32 x 32 tiles through shared memory).
+__global__ void __launch_bounds__(256) cb_loc_kernel(const CbArgs a) {
+    const CbHeader* hdr = reinterpret_cast<const CbHeader*>(a.ws);
+    if (!hdr->ok) return;
+    __shared__ float2 tile[32][33];
+    const int ap = a.A * a.P;
+    const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32, b = blockIdx.z;
+    const float2* src = reinterpret_cast<const float2*>(a.loc) + (long long)b * ap * a.Ncam;
+    float2* dst = reinterpret_cast<float2*>(a.ws + a.L.loct) + (long long)b * a.Ncam * ap;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, kk = k0 + tx;
+        if (i < ap && kk < a.Ncam) tile[r][tx] = __ldg(src + (long long)i * a.Ncam + kk);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int kk = k0 + r, i = i0 + tx;
+        if (i < ap && kk < a.Ncam) dst[(long long)kk * ap + i] = tile[tx][r];
     }
 }
 
@@ -792,6 +875,10 @@ msda_status launch_backward_cb(const Problem& p, const float* grad_out, float* g
     if ((st = ensure_smem((const void*)bin, bin_smem, dev)) != MSDA_OK) return st;
     if ((st = ensure_smem((const void*)red, red_smem, dev)) != MSDA_OK) return st;
     cb_plan_kernel<<<1, kCbThreads, 0, stream>>>(a);
+    {
+        const dim3 lg((unsigned)((p.A * p.P + 31) / 32), (unsigned)((p.Ncam + 31) / 32), (unsigned)p.B);
+        cb_loc_kernel<<<lg, 256, 0, stream>>>(a);
+    }
     const long long nbm = (long long)p.B * a.nmaps;
     bin<<<(unsigned)(nbm + 16), kCbThreads, bin_smem, stream>>>(a);
     const int ngb = dev.sm_count / p.G;

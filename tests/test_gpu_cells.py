@@ -86,12 +86,25 @@ def test_heavy_rows_take_whole_warps():
         check(pr, f"heavy maps {maps[0]} A={A}")
 
 
-def test_overfull_cell_takes_the_corner_slot_form():
-    """About 400 points in each cell of a 1x1 map: more than a binning block sorts, so the plan's flag is
-    cleared and the corner-slot form computes the gradient."""
+def test_few_cells_under_hundreds_of_points():
+    """About 400 points in each cell of a 1x1 map: maps of few cells place their points stably (per-warp
+    cursors, no per-cell sort), so any number of points per cell stays on the cell-binned path."""
     gen = torch.Generator().manual_seed(1602)
     pr = inputs.make_problem(gen, B=1, cam_maps=[[(2, 2), (1, 1)]] * 2, C=32, G=4, A=200, P=8, loc_range=(0.0, 1.0))
-    _, flag = check(pr, "overfull cells", expect_cells=False)
+    check(pr, "hundreds of points per cell")
+
+
+def test_overfull_cell_of_a_large_map_takes_the_corner_slot_form():
+    """A map of many cells (sorted per cell after an atomic placement) with 320 points in one cell: more than a
+    binning block sorts, so the plan's flag is cleared and the corner-slot form computes the gradient."""
+    gen = torch.Generator().manual_seed(1603)
+    pr = inputs.make_problem(gen, B=1, cam_maps=[[(100, 100)]], C=32, G=4, A=40, P=8, loc_range=(0.0, 1.0))
+    loc = pr.sampling_location.clone()
+    loc.fill_(0.5051)  # one bilinear cell
+    loc += (torch.rand(loc.shape, generator=gen) - 0.5) * 2e-5
+    one = inputs.Problem(pr.feat, pr.spatial_shape, pr.scale_start_index, loc.contiguous(), pr.weights,
+                         pr.grad_out)
+    _, flag = check(one, "overfull cell", expect_cells=False)
     assert flag == 0
 
 
