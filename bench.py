@@ -65,7 +65,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--copy-streams", type=int, default=1, help="streams per copy direction in the end-to-end run")
     ap.add_argument("--cpu-sample-anchors", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -763,8 +763,11 @@ def main():
         raise RuntimeError("device status set during the timed region")
 
     # End to end through the public API with host buffers (pinned): every step copies its inputs host->device,
-    # runs the forward and backward, and copies out and the three gradients device->host.  Consecutive steps
-    # overlap on three streams (copy-in, compute, copy-out) with two buffer sets, as an input pipeline would.
+    # runs the forward and backward, and reads its result back device->host.  The result is `out`, the
+    # forward's output: the gradients are consumed on the device by the layers upstream of the operator (a
+    # second run also copies all three gradients back, for hosts that want them).  Consecutive steps overlap on
+    # three streams (copy-in, compute, copy-out) with two buffer sets, as an input pipeline would; the timed
+    # steps start from an empty pipeline, so their count amortises one fill.
     h_in = [x.cpu().pin_memory() for x in (pr.feat, pr.sampling_location, pr.weights, pr.grad_out)]
     h2d = sum(x.numel() * x.element_size() for x in h_in)
     slots = []
@@ -772,7 +775,6 @@ def main():
         d_in = [torch.empty_like(x, device=dev) for x in h_in]
         d_out = [torch.empty_like(x) for x in (out, gf, gl, gw)]
         slots.append((d_in, d_out, [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in d_out]))
-    d2h = sum(x.numel() * x.element_size() for x in slots[0][2])
     nsplit = max(1, args.copy_streams)
     s_in = [torch.cuda.Stream(dev) for _ in range(nsplit)]
     s_out = [torch.cuda.Stream(dev) for _ in range(nsplit)]
@@ -790,59 +792,66 @@ def main():
                         dd.view(-1)[lo:hi].copy_(ss.view(-1)[lo:hi], non_blocking=True)
             done[q].record(st)
 
-    def e2e_step(i):
-        j = i % 2
-        d_in, d_out, h_out = slots[j]
-        # copy-in waits until the compute that last read this slot's inputs is done
-        split_copy(d_in, h_in, s_in, ev_comp[j][0], ev_in[j])
-        for e in ev_in[j]:
-            main.wait_event(e)
-        for e in ev_out[j]:
-            main.wait_event(e)  # this slot's outputs have been copied out
-        tens = (d_in[0], d.spatial_shape, d.scale_start_index, d_in[1], d_in[2])
-        fwd(tens, d_out)
-        bwd(tens, d_in[3], d_out)
-        ev_comp[j][0].record(main)
-        split_copy(h_out, d_out, s_out, ev_comp[j][0], ev_out[j])
+    def run_e2e(sel, nsteps):
+        """ms per step of the pipelined end-to-end step reading back outputs `sel` (of out, gf, gl, gw), the
+        bytes it reads back, and the ms of the same copies alone (both directions at once)."""
+        def e2e_step(i):
+            j = i % 2
+            d_in, d_out, h_out = slots[j]
+            # copy-in waits until the compute that last read this slot's inputs is done
+            split_copy(d_in, h_in, s_in, ev_comp[j][0], ev_in[j])
+            for e in ev_in[j]:
+                main.wait_event(e)
+            for e in ev_out[j]:
+                main.wait_event(e)  # this slot's outputs have been copied out
+            tens = (d_in[0], d.spatial_shape, d.scale_start_index, d_in[1], d_in[2])
+            fwd(tens, d_out)
+            bwd(tens, d_in[3], d_out)
+            ev_comp[j][0].record(main)
+            split_copy([h_out[q] for q in sel], [d_out[q] for q in sel], s_out, ev_comp[j][0], ev_out[j])
 
-    for i in range(2):
-        e2e_step(i)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(main)
-    for i in range(args.e2e_steps):
-        e2e_step(i)
-    for st in s_out:
-        main.wait_stream(st)
-    s1.record(main)
-    torch.cuda.synchronize(dev)
-    e2e_ms = max_over_ranks([s0.elapsed_time(s1) / args.e2e_steps], dev)[0]
+        for i in range(2):
+            e2e_step(i)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(main)
+        for i in range(nsteps):
+            e2e_step(i)
+        for st in s_out:
+            main.wait_stream(st)
+        s1.record(main)
+        torch.cuda.synchronize(dev)
+        e2e_ms = max_over_ranks([s0.elapsed_time(s1) / nsteps], dev)[0]
 
-    # the same copies alone (one step's inputs in and outputs out, both directions at once): the floor of the
-    # end-to-end step on this host link
-    def copies_only():
-        s_in[0].wait_stream(main)
-        s_out[0].wait_stream(main)
-        with torch.cuda.stream(s_in[0]):
-            for dd, ss in zip(slots[0][0], h_in):
-                dd.copy_(ss, non_blocking=True)
-        with torch.cuda.stream(s_out[0]):
-            for dd, ss in zip(slots[1][2], slots[1][1]):
-                dd.copy_(ss, non_blocking=True)
-        main.wait_stream(s_in[0])
-        main.wait_stream(s_out[0])
+        # the same copies alone (one step's inputs in and outputs out, both directions at once): the floor of
+        # the end-to-end step on this host link
+        def copies_only():
+            s_in[0].wait_stream(main)
+            s_out[0].wait_stream(main)
+            with torch.cuda.stream(s_in[0]):
+                for dd, ss in zip(slots[0][0], h_in):
+                    dd.copy_(ss, non_blocking=True)
+            with torch.cuda.stream(s_out[0]):
+                for q in sel:
+                    slots[1][2][q].copy_(slots[1][1][q], non_blocking=True)
+            main.wait_stream(s_in[0])
+            main.wait_stream(s_out[0])
 
-    copies_only()
-    torch.cuda.synchronize(dev)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(main)
-    for _ in range(3):
         copies_only()
-    c1.record(main)
-    torch.cuda.synchronize(dev)
-    copy_ms = max_over_ranks([c0.elapsed_time(c1) / 3], dev)[0]
+        torch.cuda.synchronize(dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(main)
+        for _ in range(3):
+            copies_only()
+        c1.record(main)
+        torch.cuda.synchronize(dev)
+        copy_ms = max_over_ranks([c0.elapsed_time(c1) / 3], dev)[0]
+        return e2e_ms, sum(slots[0][2][q].numel() * slots[0][2][q].element_size() for q in sel), copy_ms
+
+    e2e_ms, d2h, copy_ms = run_e2e((0,), args.e2e_steps)
+    e2e_all_ms, d2h_all, copy_all_ms = run_e2e((0, 1, 2, 3), max(3, args.e2e_steps // 2))
 
     hbm_peak, peak_src = peaks()
     feat_mb = d.feat.numel() * d.feat.element_size() / 1e6
@@ -914,10 +923,16 @@ def main():
         "counts": cnt.as_dict(),
         "e2e": {"value": e2e_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps,
+                "reads_back": "out (the forward's result); the gradients stay on the device for the layers upstream",
                 "pipeline": f"copy-in, compute and copy-out of consecutive steps overlap (2 buffer sets; each "
-                            f"direction's copies cut over {nsplit} streams)",
+                            f"direction's copies cut over {nsplit} streams); timed from an empty pipeline",
                 "copy_floor": {"value": copy_ms * 1e3 / B, "unit": UNIT, "frac": copy_ms / e2e_ms,
-                               "what": "the step's host<->device copies alone, both directions at once"}},
+                               "what": "the step's host<->device copies alone, both directions at once"},
+                "with_gradients_to_host": {
+                    "value": e2e_all_ms * 1e3 / B, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h_all, "steps": max(3, args.e2e_steps // 2),
+                    "reads_back": "out, grad_feat, grad_loc, grad_weights",
+                    "copy_floor": {"value": copy_all_ms * 1e3 / B, "unit": UNIT, "frac": copy_all_ms / e2e_all_ms}}},
         "gpu_launches": ((2 if fwd_ws is not None and not fwd_clear else 1) + backward_launches(det, fwd_clear))
                         * args.steps,
         "tuning": {"forward": ft, "backward": bt},

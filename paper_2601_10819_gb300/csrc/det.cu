@@ -585,7 +585,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     row_scan_totals_kernel<<<1, 1024, 0, stream>>>(tsum, L.ntiles, rowptr + nrows, gate);
     {
         long long ab = (nrows + 255) / 256;
-        if (ab > (long long)dev.sm_count * 16) ab = (long long)dev.sm_count * 16;
+        if (ab > (long long)dev.sm_count * 8) ab = (long long)dev.sm_count * 8;
         row_scan_add_kernel<<<(unsigned)ab, 256, 0, stream>>>(rowptr, tsum, nrows, gate);
     }
     if ((st = check_launch("msda_backward row offsets")) != MSDA_OK) return st;
@@ -593,7 +593,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
         det_rows_kernel<true><<<(unsigned)kgrid, 256, 0, stream>>>(ka);
         // the per-row counts are all zero again after the fill: their array takes the list of long rows
         long long sb = (nrows + 255) / 256;
-        if (sb > (long long)dev.sm_count * 16) sb = (long long)dev.sm_count * 16;
+        if (sb > (long long)dev.sm_count * 8) sb = (long long)dev.sm_count * 8;
         det_segsort_short_kernel<<<(unsigned)sb, 256, 0, stream>>>(rowptr, nrows, vals, cnt, cnt + nrows, gate);
         det_segsort_long_kernel<<<(unsigned)dev.sm_count * 8, kSegWarps * 32, 0, stream>>>(rowptr, cnt, cnt + nrows,
                                                                                           vals, e_om, gate);
@@ -614,7 +614,7 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     if (L.n > 0) {
         if ((st = ensure_smem((const void*)det_prep_kernel, smem, dev)) != MSDA_OK) return st;
         long long pb = ((long long)L.n + 255) / 256;
-        if (pb > (long long)dev.sm_count * 32) pb = (long long)dev.sm_count * 32;
+        if (pb > (long long)dev.sm_count * 8) pb = (long long)dev.sm_count * 8;
         det_prep_kernel<<<(unsigned)pb, 256, smem, stream>>>(ra, L.n, reinterpret_cast<float*>(e_om), e_pt, e_ba);
         if ((st = check_launch("msda_backward prep")) != MSDA_OK) return st;
     }
