@@ -646,7 +646,7 @@ def run_reference(args, rank, world):
                                        f"single-threaded), scaled to a frame by {A}/{na}"},
             # value and ms_per_step are a frame's time extrapolated from the anchor sample, not the wall time of
             # a step; measured_ms_per_step is the sample's own time
-            "extrapolated": True, "frame_scale": A / na,
+            "extrapolated": na < A, "frame_scale": A / na,
             "measured_ms_per_step": statistics.mean(raw) * 1e3,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

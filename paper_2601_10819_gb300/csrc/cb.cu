@@ -36,6 +36,7 @@ constexpr int kCbHeavyPerRow = 32;   // expected contributions per row from whic
 constexpr unsigned short kNoCell = 0xffffu;
 constexpr int kCbMaxBin = 256;       // points one cell may hold (more: the corner-slot path takes over)
 constexpr int kCbMaxRows = 1024;     // image rows of a map the reduce's band planner holds
+constexpr int kCbDirect = 1 << 30;   // band-end flag: the band is read in place, not staged
 
 struct CbMap {
     int H, W, start;  // W == 0: the map is invalid and skipped
@@ -503,12 +504,6 @@ __global__ void __launch_bounds__(kCbThreads, 2) cb_bin_kernel(const CbArgs a) {
             else s_abort = 1;
         }
     }
-    // one image row's band (cell rows i-1 and i) must fit a reduce band buffer
-    for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        const int r0 = i * W1, r2 = (i + 2) * W1;  // first cells of cell rows i - 1 and i + 1
-        const uint32_t s0 = r0 > 0 ? cend[r0 - 1] : 0u, s2 = cend[r2 - 1];
-        if ((int)(s2 - s0) > a.nb - 8) s_abort = 1;
-    }
     __syncthreads();
     if (s_abort) {
         if (threadIdx.x == 0) atomicExch(&hdr->ok, 0);
@@ -657,7 +652,10 @@ __device__ __forceinline__ void cb_step(const uint32_t* __restrict__ Ao, const f
 
 // Band copies of one map: band k covers image rows [i0, i1), so cell rows i0 - 1 .. i1 - 1: their records
 // [rp[i0], rp[i1 + 1]) (coefficients of group g and anchor offsets) and their cell pointers, the pointer and
-// offset ranges rounded out to 16 bytes.  Issued by one thread; completes on `bar`.
+// offset ranges rounded out to 16 bytes.  Issued by one thread; completes on `bar`.  A band whose end carries
+// kCbDirect holds rows of which even one exceeds a buffer (cells of hundreds of points in a coarse map): the
+// sweep reads its records and cell pointers from the workspace itself, and its barrier phase completes with a
+// plain arrival, so the buffers' phases stay in step.
 struct CbBand {
     uint32_t e0, ea0, ca0;  // first record, first staged anchor-offset slot, first staged cell pointer
 };
@@ -666,6 +664,11 @@ __device__ __forceinline__ CbBand cb_issue_band(const CbArgs& a, unsigned char* 
                                                 const uint32_t* rp, int i0, int i1, long long pm, int W1,
                                                 const float4* coef_g, uint64_t* bar) {
     CbBand bd;
+    if (i1 & kCbDirect) {  // read in place from the workspace: nothing to copy, the phase completes at once
+        mbar_arrive(bar);
+        bd.e0 = bd.ea0 = bd.ca0 = 0u;
+        return bd;
+    }
     const uint32_t e0 = rp[i0], e1 = rp[i1 + 1];
     const uint32_t ea0 = e0 & ~3u, ea1 = (e1 + 3u) & ~3u;
     const long long c0 = pm + (long long)i0 * W1, c1 = pm + (long long)(i1 + 1) * W1 + 1;
@@ -682,6 +685,50 @@ __device__ __forceinline__ CbBand cb_issue_band(const CbArgs& a, unsigned char* 
     bd.ea0 = ea0;
     bd.ca0 = (uint32_t)ca0;
     return bd;
+}
+
+// The column sweeps of a band read in place: the same steps as the staged sweep in cb_reduce_kernel, with the
+// records, anchor offsets and cell pointers taken from the workspace (record e, anchor offset e, cell pointer c
+// at their own indices).  Kept out of line so the staged sweep, which nearly every band takes, is compiled
+// as if it were alone.
+template <int LG>
+__device__ __noinline__ void cb_sweep_in_place(const CbArgs& a, const float4* __restrict__ coef_g,
+                                               const float4* __restrict__ sgo, float* gfm, long long pm, int i0,
+                                               int i1, int W, int seg, int ntask, bool heavy, int l, int lgi, int t0,
+                                               int tstep, bool failed) {
+    constexpr int NLGW = 32 / LG;
+    const int W1 = W + 1;
+    const int off = heavy ? lgi : 0, step = heavy ? NLGW : 1;
+    const uint32_t* Ao = reinterpret_cast<const uint32_t*>(a.ws + a.L.aoff);
+    const uint32_t* Cp = reinterpret_cast<const uint32_t*>(a.ws + a.L.cellptr);
+    for (int task = t0; task < ntask && !failed; task += tstep) {
+        const int sg = task / W, j = task - sg * W;
+        const int r0 = i0 + sg * seg, r1 = min(r0 + seg, i1);
+        if (r0 >= r1) continue;
+        float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), nxt = cur;
+        long long ci = pm + (long long)r0 * W1 + j;  // left cell of cell row r0 - 1
+        for (int cy = r0 - 1; cy < r1; ++cy) {
+            const uint32_t q0 = Cp[ci], q1 = Cp[ci + 1], q2 = Cp[ci + 2];
+            if (cy < r0) {
+                cb_step<true>(Ao, coef_g, sgo, l, q0 + off, q1, q2, 0u, 0u, step, cur, nxt);
+            } else {
+                cb_step<false>(Ao, coef_g, sgo, l, q0 + off, q1, q2, 0u, 0u, step, cur, nxt);
+                if (heavy) {
+#pragma unroll
+                    for (int o = LG; o < 32; o <<= 1) {
+                        cur.x += __shfl_xor_sync(0xffffffffu, cur.x, o);
+                        cur.y += __shfl_xor_sync(0xffffffffu, cur.y, o);
+                        cur.z += __shfl_xor_sync(0xffffffffu, cur.z, o);
+                        cur.w += __shfl_xor_sync(0xffffffffu, cur.w, o);
+                    }
+                }
+                if (!heavy || lgi == 0) *reinterpret_cast<float4*>(gfm + ((long long)cy * W + j) * a.C) = cur;
+            }
+            cur = nxt;
+            nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+            ci += W1;
+        }
+    }
 }
 
 template <int LG>
@@ -751,8 +798,15 @@ __global__ void __launch_bounds__(kCbThreads, 1) cb_reduce_kernel(const CbArgs a
                             if (bal) i1 = i0 + base + 31 - __clz(bal);
                             if (bal != 0xffffffffu) break;
                         }
-                        if (i1 == i0) i1 = i0 + 1;  // cannot happen: the binning checked that one row fits
-                        if (lane == 0) bend[nb] = i1;
+                        int flag = 0;
+                        if (i1 == i0) {
+                            // row i0 alone (cell rows i0 - 1 and i0) exceeds a buffer: it and the rows after it that
+                            // do too form one band read in place
+                            i1 = i0 + 1;
+                            while (i1 < H && (int)(rp[i1 + 2] - rp[i1]) > a.nb - 8) ++i1;
+                            flag = kCbDirect;
+                        }
+                        if (lane == 0) bend[nb] = i1 | flag;
                         ++nb;
                         i0 = i1;
                     }
@@ -762,8 +816,8 @@ __global__ void __launch_bounds__(kCbThreads, 1) cb_reduce_kernel(const CbArgs a
                 const int nb = s_nb;
                 if (threadIdx.x == 0) {
                     for (int k = 0; k < 2 && k < nb; ++k)
-                        s_band[k] = cb_issue_band(a, buf0 + k * L.bsize, L, rp, k ? bend[k - 1] : 0, bend[k], pm, W1,
-                                                  coef_g, &mbar[k]);
+                        s_band[k] = cb_issue_band(a, buf0 + k * L.bsize, L, rp, k ? bend[k - 1] & ~kCbDirect : 0,
+                                                  bend[k], pm, W1, coef_g, &mbar[k]);
                 }
                 float* gfm = gfb + (long long)mp.start * a.C;
                 const bool heavy = mp.heavy != 0;
@@ -777,12 +831,10 @@ __global__ void __launch_bounds__(kCbThreads, 1) cb_reduce_kernel(const CbArgs a
                     }
                     __syncthreads();
                     if (bf) ph1 ^= 1u; else ph0 ^= 1u;
-                    const int i0 = k ? bend[k - 1] : 0, i1 = bend[k];
+                    const int i0 = k ? bend[k - 1] & ~kCbDirect : 0, i1 = bend[k] & ~kCbDirect;
+                    const bool direct = (bend[k] & kCbDirect) != 0;
                     const CbBand bd = s_band[bf];
                     const unsigned char* bb = buf0 + bf * L.bsize;
-                    const float4* Cf = reinterpret_cast<const float4*>(bb);
-                    const uint32_t* Ao = reinterpret_cast<const uint32_t*>(bb + L.aoff);
-                    const uint32_t* Cp = reinterpret_cast<const uint32_t*>(bb + L.cptr);
                     const int R = i1 - i0;
                     const int slots = heavy ? kCbWarps : nlg;
                     int S = slots / W;
@@ -792,40 +844,48 @@ __global__ void __launch_bounds__(kCbThreads, 1) cb_reduce_kernel(const CbArgs a
                     const int t0 = heavy ? warp : lgid, tstep = heavy ? kCbWarps : nlg;
                     const int off = heavy ? lgi : 0, step = heavy ? NLGW : 1;
                     const bool failed = s_fail != 0;
-                    for (int task = t0; task < ntask && !failed; task += tstep) {
-                        const int sg = task / W, j = task - sg * W;
-                        const int r0 = i0 + sg * seg, r1 = min(r0 + seg, i1);
-                        if (r0 >= r1) continue;
-                        float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), nxt = cur;
-                        // left cell of cell row r0 - 1 (cell row index r0), as a slot of the staged pointers
-                        int ci = (int)(pm - (long long)bd.ca0) + r0 * W1 + j;
-                        for (int cy = r0 - 1; cy < r1; ++cy) {
-                            const uint32_t q0 = Cp[ci], q1 = Cp[ci + 1], q2 = Cp[ci + 2];
-                            if (cy < r0) {
-                                cb_step<true>(Ao, Cf, sgo, l, q0 + off, q1, q2, bd.ea0, bd.e0, step, cur, nxt);
-                            } else {
-                                cb_step<false>(Ao, Cf, sgo, l, q0 + off, q1, q2, bd.ea0, bd.e0, step, cur, nxt);
-                                if (heavy) {
+                    if (direct) {
+                        cb_sweep_in_place<LG>(a, coef_g, sgo, gfm, pm, i0, i1, W, seg, ntask, heavy, l, lgi,
+                                              t0, tstep, failed);
+                    } else {
+                        const float4* Cf = reinterpret_cast<const float4*>(bb);
+                        const uint32_t* Ao = reinterpret_cast<const uint32_t*>(bb + L.aoff);
+                        const uint32_t* Cp = reinterpret_cast<const uint32_t*>(bb + L.cptr);
+                        for (int task = t0; task < ntask && !failed; task += tstep) {
+                            const int sg = task / W, j = task - sg * W;
+                            const int r0 = i0 + sg * seg, r1 = min(r0 + seg, i1);
+                            if (r0 >= r1) continue;
+                            float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), nxt = cur;
+                            // left cell of cell row r0 - 1 (cell row index r0), as a slot of the staged pointers
+                            int ci = (int)(pm - (long long)bd.ca0) + r0 * W1 + j;
+                            for (int cy = r0 - 1; cy < r1; ++cy) {
+                                const uint32_t q0 = Cp[ci], q1 = Cp[ci + 1], q2 = Cp[ci + 2];
+                                if (cy < r0) {
+                                    cb_step<true>(Ao, Cf, sgo, l, q0 + off, q1, q2, bd.ea0, bd.e0, step, cur, nxt);
+                                } else {
+                                    cb_step<false>(Ao, Cf, sgo, l, q0 + off, q1, q2, bd.ea0, bd.e0, step, cur, nxt);
+                                    if (heavy) {
 #pragma unroll
-                                    for (int o = LG; o < 32; o <<= 1) {
-                                        cur.x += __shfl_xor_sync(0xffffffffu, cur.x, o);
-                                        cur.y += __shfl_xor_sync(0xffffffffu, cur.y, o);
-                                        cur.z += __shfl_xor_sync(0xffffffffu, cur.z, o);
-                                        cur.w += __shfl_xor_sync(0xffffffffu, cur.w, o);
+                                        for (int o = LG; o < 32; o <<= 1) {
+                                            cur.x += __shfl_xor_sync(0xffffffffu, cur.x, o);
+                                            cur.y += __shfl_xor_sync(0xffffffffu, cur.y, o);
+                                            cur.z += __shfl_xor_sync(0xffffffffu, cur.z, o);
+                                            cur.w += __shfl_xor_sync(0xffffffffu, cur.w, o);
+                                        }
                                     }
+                                    if (!heavy || lgi == 0)
+                                        *reinterpret_cast<float4*>(gfm + ((long long)cy * W + j) * a.C) = cur;
                                 }
-                                if (!heavy || lgi == 0)
-                                    *reinterpret_cast<float4*>(gfm + ((long long)cy * W + j) * a.C) = cur;
+                                cur = nxt;
+                                nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+                                ci += W1;
                             }
-                            cur = nxt;
-                            nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-                            ci += W1;
                         }
                     }
                     __syncthreads();  // the buffer is free again
                     if (threadIdx.x == 0 && k + 2 < nb)
-                        s_band[bf] = cb_issue_band(a, buf0 + bf * L.bsize, L, rp, bend[k + 1], bend[k + 2], pm, W1,
-                                                   coef_g, &mbar[bf]);
+                        s_band[bf] = cb_issue_band(a, buf0 + bf * L.bsize, L, rp, bend[k + 1] & ~kCbDirect,
+                                                   bend[k + 2], pm, W1, coef_g, &mbar[bf]);
                 }
             }
             __syncthreads();  // every thread has read s_item[cur_slot] and finished the map

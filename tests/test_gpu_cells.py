@@ -94,6 +94,15 @@ def test_few_cells_under_hundreds_of_points():
     check(pr, "hundreds of points per cell")
 
 
+def test_dense_coarse_map_reads_its_bands_in_place():
+    """3600 points in a 2x3 map with 900 anchors' grad_out staged: the records of one image row (two cell rows,
+    about 2400) exceed a band buffer, so that band is swept from the workspace in place, not staged."""
+    gen = torch.Generator().manual_seed(1604)
+    pr = inputs.make_problem(gen, B=1, cam_maps=[[(2, 3), (1, 2)]], C=256, G=8, A=900, P=4, loc_range=(0.0, 1.0),
+                             feat_dtype="bf16", w_dtype="bf16")
+    check(pr, "dense coarse map, bands in place")
+
+
 def test_overfull_cell_of_a_large_map_takes_the_corner_slot_form():
     """A map of many cells (sorted per cell after an atomic placement) with 320 points in one cell: more than a
     binning block sorts, so the plan's flag is cleared and the corner-slot form computes the gradient."""
@@ -161,6 +170,20 @@ def test_too_many_points_per_camera_take_the_corner_slot_form():
     ref = oracle_backward(pr)
     errs = [relerr(x.double().numpy(), r) for x, r in zip(g, ref)]
     assert max(errs) <= TOL_FP32, errs
+
+
+def test_train_16cam_full_size_takes_the_cells():
+    """The 16-camera B = 4 batch at full size: its 8x22 maps hold about 11 000 points per camera (bands in place),
+    the cell-binned path runs for the whole call and agrees with the corner-slot form (the per-frame oracle
+    comparison of both is in test_gpu_backward)."""
+    pr = inputs.make_workload(3)
+    (gf, gl, gw), flag = run(pr)
+    assert flag == 1
+    (cf, cl, cw), _ = run(pr, variant=5)
+    for name, x, y in (("dfeat", gf, cf), ("dloc", gl, cl), ("dw", gw, cw)):
+        e = relerr(x.double().numpy(), y.double().numpy())
+        print(f"train-16cam cells vs corner-slot {name} rel diff {e:.2e}")
+        assert e <= TOL_FP32
 
 
 def test_outside_in_64cam_full_size_cells_against_oracle():
