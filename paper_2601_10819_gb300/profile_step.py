@@ -1,6 +1,7 @@
 """Run the operator's training step a fixed number of times, for a profiler.
 
     python -m paper_2601_10819_gb300.profile_step --workload outside-in-64cam --steps 3 --warps 8 --vec 2
+    python -m paper_2601_10819_gb300.profile_step --workload outside-in-64cam --ncam 32 --steps 2   # half the maps
 
 Each step is one msda_forward and one msda_backward (deterministic by default, ``--atomic`` for the
 atomic mode; ``--forward-only`` drops the backward) on a seeded synthetic workload, with an explicit launch
@@ -31,12 +32,15 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warps", type=int, default=8, help="warps per block (forward and backward)")
     ap.add_argument("--vec", type=int, default=2, help="16-byte vectors per lane")
+    ap.add_argument("--ncam", type=int, default=None, help="fewer cameras (64- and 16-camera workloads)")
+    ap.add_argument("--batch", type=int, default=None, help="fewer frames (16-camera workload)")
     ap.add_argument("--atomic", action="store_true", help="atomic backward instead of the deterministic one")
     ap.add_argument("--forward-only", action="store_true")
     args = ap.parse_args(argv)
 
     idx, fdt, wdt = WORKLOADS[args.workload]
-    pr = inputs.make_workload(idx, feat_dtype=fdt, w_dtype=wdt, with_grad=not args.forward_only).to("cuda")
+    pr = inputs.make_workload(idx, feat_dtype=fdt, w_dtype=wdt, with_grad=not args.forward_only, ncam=args.ncam,
+                              batch=args.batch).to("cuda")
     T = pr.tensors()
     B, sum_hw, C = pr.feat.shape
     _, A, P, K, _ = pr.sampling_location.shape
@@ -55,7 +59,7 @@ def main(argv=None) -> int:
                           vec=args.vec)
     torch.cuda.synchronize()
     status = msda.device_status()
-    print(f"{args.workload}: {args.steps} steps, device status {status}")
+    print(f"{args.workload} (B={B}, {K} cameras): {args.steps} steps, device status {status}")
     return 0 if status == 0 else 1
 
 
