@@ -420,12 +420,13 @@ class MSDAFunction(torch.autograd.Function):
     """Differentiable MSDA: gradients for feat, sampling_location and weights.
 
     The forward output is float32; the gradients are float32 and are cast to
-    the input dtypes when those are reduced precision.
+    the input dtypes when those are reduced precision.  The backward is the
+    deterministic mode unless deterministic=False (the atomic mode).
     """
 
     @staticmethod
     def forward(ctx, feat, spatial_shape, scale_start_index, sampling_location, weights,
-                deterministic: bool = False):
+                deterministic: bool = True):
         ctx.save_for_backward(feat, spatial_shape, scale_start_index, sampling_location, weights)
         ctx.deterministic = bool(deterministic)
         return forward(feat, spatial_shape, scale_start_index, sampling_location, weights)
@@ -440,6 +441,6 @@ class MSDAFunction(torch.autograd.Function):
                 gw.to(w.dtype) if ctx.needs_input_grad[4] else None, None)
 
 
-def msda(feat, spatial_shape, scale_start_index, sampling_location, weights, deterministic: bool = False):
+def msda(feat, spatial_shape, scale_start_index, sampling_location, weights, deterministic: bool = True):
     """Differentiable entry point (see MSDAFunction)."""
     return MSDAFunction.apply(feat, spatial_shape, scale_start_index, sampling_location, weights, deterministic)

@@ -147,9 +147,14 @@ def test_autograd_function_matches_direct_calls_and_gradcheck():
     out = msda.msda(feat, d.spatial_shape, d.scale_start_index, loc, w)
     out.backward(d.grad_out)
     gf, gl, gw = msda.backward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights,
-                               d.grad_out)
-    assert torch.equal(w.grad, gw) and torch.equal(loc.grad, gl)  # no atomics: bitwise
-    assert relerr(feat.grad.cpu().double().numpy(), gf.cpu().double().numpy()) <= 1e-6  # atomic order varies
+                               d.grad_out, deterministic=True)
+    # the autograd function's default backward is the deterministic mode: bitwise the direct call
+    assert torch.equal(w.grad, gw) and torch.equal(loc.grad, gl) and torch.equal(feat.grad, gf)
+    feat.grad = loc.grad = w.grad = None
+    msda.msda(feat, d.spatial_shape, d.scale_start_index, loc, w, False).backward(d.grad_out)
+    ga = msda.backward(d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights, d.grad_out)
+    assert torch.equal(w.grad, ga[2]) and torch.equal(loc.grad, ga[1])  # no atomics in dloc, dw
+    assert relerr(feat.grad.cpu().double().numpy(), ga[0].cpu().double().numpy()) <= 1e-6  # atomic order varies
     # the operator is linear in feat and weights: finite differences are exact up to rounding
     f0 = d.feat.clone().requires_grad_()
     w0 = d.weights.clone().requires_grad_()

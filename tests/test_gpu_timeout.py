@@ -10,7 +10,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import TOL_FP32, ensure_lib, oracle_backward, oracle_forward, relerr
+from gpu_util import TOL_FP32, TOL_LOWP_GRAD, ensure_lib, oracle_backward, oracle_forward, relerr
 from paper_2601_10819_gb300 import inputs, msda
 
 pytestmark = pytest.mark.gpu
@@ -63,3 +63,15 @@ def test_staged_deterministic_backward(variant):
     g = gives_up_then_recovers(lambda: msda.backward(*T, d.grad_out, deterministic=True, variant=variant))
     for x, r in zip(g, oracle_backward(pr)):
         assert relerr(x.cpu().double().numpy(), r) <= TOL_FP32
+
+
+def test_bands_read_in_place_give_up_then_recover():
+    """A dense coarse map whose bands exceed a buffer and are swept in place: their barrier phase completes with a
+    plain arrival, and the give-up path and the recovery behave as for staged bands."""
+    gen = torch.Generator().manual_seed(1604)
+    pr = inputs.make_problem(gen, B=1, cam_maps=[[(2, 3), (1, 2)]], C=256, G=8, A=900, P=4, loc_range=(0.0, 1.0),
+                             feat_dtype="bf16", w_dtype="bf16")
+    d, T = tensors(pr)
+    g = gives_up_then_recovers(lambda: msda.backward(*T, d.grad_out, deterministic=True))
+    for x, r in zip(g, oracle_backward(pr)):
+        assert relerr(x.cpu().double().numpy(), r) <= TOL_LOWP_GRAD
