@@ -5,6 +5,8 @@ feature row summed over its four cells' bins with grad_out staged per channel gr
 disjoint and the sizes fit; the first int of its workspace is the plan's flag, 1 when that path ran.
 tuning variant 5 forces the corner-slot path on the same inputs.
 """
+import random
+
 import numpy as np
 import pytest
 import torch
@@ -196,3 +198,26 @@ def test_outside_in_64cam_full_size_cells_against_oracle():
         e = relerr(x.double().numpy(), r)
         print(f"outside-in-64cam cells {name} rel err {e:.2e}")
         assert e <= TOL_LOWP_GRAD
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_problems(seed):
+    """Seeded random problems: 1-5 cameras of 1-4 maps of 1..40 x 1..40 pixels each, several channel groupings and
+    dtype pairs, 1-200 anchors of 1-8 keypoints, B = 1..3, location ranges from narrow (dense cells, heavy maps)
+    to wide (points across and beyond the borders), some pairs out of view. Whichever deterministic form runs (the
+    cell-binned one, unless a check sends the call to the corner-slot one), it must match the oracle, the other
+    form and itself, bitwise."""
+    rng = random.Random(seed)
+    gen = torch.Generator().manual_seed(10_000 + seed)
+    ncam, nscale = rng.randint(1, 5), rng.randint(1, 4)
+    maps = [[(rng.randint(1, 40), rng.randint(1, 40)) for _ in range(nscale)] for _ in range(ncam)]
+    C, G, fdt = rng.choice([(32, 4, "f32"), (64, 8, "bf16"), (128, 4, "bf16"), (256, 8, "bf16"), (64, 2, "f32"),
+                            (256, 8, "f16")])
+    wdt = fdt if rng.random() < 0.7 else "f32"
+    lo = rng.uniform(-0.3, 0.6)
+    hi = max(lo + rng.choice([rng.uniform(0.02, 0.2), rng.uniform(0.5, 1.6)]), 0.05)
+    pr = inputs.make_problem(gen, B=rng.randint(1, 3), cam_maps=maps, C=C, G=G, A=rng.randint(1, 200),
+                             P=rng.randint(1, 8), loc_range=(lo, hi), out_frac=rng.choice([0.0, 0.0, 0.3]),
+                             feat_dtype=fdt, w_dtype=wdt)
+    check(pr, f"random {seed}: {ncam}x{nscale} maps, C={C} G={G} {fdt}/{wdt}, loc ({lo:.2f}, {hi:.2f})",
+          expect_cells=False)
