@@ -258,13 +258,9 @@ def l2_rates(dev, stream, tries=5):
     return gather, red
 
 
-def oracle_times(pr, sample_anchors):
-    """Seconds per frame of the FP64 oracle on the first `sample_anchors` anchors, scaled to all anchors:
-    forward on all host threads and on one, backward on one."""
+def _oracle_calls(sub, nthreads):
+    """Seconds of one oracle call each on `sub`: forward on `nthreads` threads, backward, forward on one thread."""
     import oracle
-    oracle.build()
-    nthreads = oracle.max_threads()
-    sub = pr.anchors(range(min(sample_anchors, pr.sampling_location.shape[1])))
     args = [oracle._f64(t) if i in (0, 3, 4) else oracle._i32(t) for i, t in enumerate(sub.tensors())]
     go = oracle._f64(sub.grad_out)
     t0 = time.perf_counter()
@@ -274,9 +270,24 @@ def oracle_times(pr, sample_anchors):
     t2 = time.perf_counter()
     oracle.forward(*args, nthreads=1)
     t3 = time.perf_counter()
-    scale = pr.sampling_location.shape[1] / sub.sampling_location.shape[1] / pr.feat.shape[0]
-    return {"fwd_all": (t1 - t0) * scale, "bwd_1": (t2 - t1) * scale, "fwd_1": (t3 - t2) * scale,
-            "raw": (t1 - t0, t2 - t1), "threads": nthreads, "anchors": sub.sampling_location.shape[1]}
+    return t1 - t0, t2 - t1, t3 - t2
+
+
+def oracle_times(pr, sample_anchors):
+    """Seconds per frame of the FP64 oracle, extrapolated from a sample of the first `sample_anchors` anchors:
+    forward on all host threads and on one, backward on one.  A call costs a fixed part (the backward allocates and
+    clears the FP64 feature gradient, whatever the anchor count) plus a part per anchor, so each call is also timed
+    on one anchor and a frame's time is fixed + (sample - fixed) * (A - 1) / (sample anchors - 1)."""
+    import oracle
+    oracle.build()
+    nthreads = oracle.max_threads()
+    A, B = pr.sampling_location.shape[1], pr.feat.shape[0]
+    na = max(2, min(sample_anchors, A))
+    one = _oracle_calls(pr.anchors(range(1)), nthreads)
+    big = _oracle_calls(pr.anchors(range(na)), nthreads)
+    frame = [(t1 + (tn - t1) * (A - 1) / (na - 1)) / B for t1, tn in zip(one, big)]
+    return {"fwd_all": frame[0], "bwd_1": frame[1], "fwd_1": frame[2], "raw": big[:2], "fixed": one[:2],
+            "threads": nthreads, "anchors": na}
 
 
 def cpu_baseline(pr, sample_anchors, others=False):
@@ -287,7 +298,9 @@ def cpu_baseline(pr, sample_anchors, others=False):
     per_frame_s = t["fwd_all"] + t["bwd_1"]
     res = {"value": per_frame_s * 1e6, "unit": UNIT, "cores": t["threads"], "kind": "oracle",
            "sample": f"{t['anchors']} of {A} anchors of one frame (fwd on {t['threads']} OpenMP threads, bwd "
-                     f"single-threaded), fwd {t['raw'][0]:.2f} s + bwd {t['raw'][1]:.2f} s, scaled by {A}/{t['anchors']}",
+                     f"single-threaded): fwd {t['raw'][0]:.2f} s + bwd {t['raw'][1]:.2f} s, of which fwd "
+                     f"{t['fixed'][0]:.2f} s + bwd {t['fixed'][1]:.2f} s is the per-call cost (timed on one anchor); "
+                     f"the per-anchor part scaled to {A} anchors",
            "fwd_us_per_frame_all_cores": t["fwd_all"] * 1e6,
            "fwd_us_per_frame_1_core": t["fwd_1"] * 1e6,
            "bwd_us_per_frame_1_core": t["bwd_1"] * 1e6,
@@ -619,22 +632,28 @@ def run_reference(args, rank, world):
     nthreads = oracle.max_threads()
     feat = oracle._f64(pr.feat)
     shape, start = oracle._i32(pr.spatial_shape), oracle._i32(pr.scale_start_index)
-    # size each step's anchor sample so that the whole run stays within ~2 minutes
-    budget_s = 120.0
-    per_anchor_s = 0.02
-    na = int(max(1, min(A, budget_s / max(1, args.steps + args.warmup) / per_anchor_s)))
-    times, raw = [], []
-    for it in range(args.warmup + args.steps):
-        a0 = (it * na) % A
-        idx = [(a0 + j) % A for j in range(na)]
+    def step(idx):
         sub = pr.anchors(idx)
         loc, w, go = oracle._f64(sub.sampling_location), oracle._f64(sub.weights), oracle._f64(sub.grad_out)
         t0 = time.perf_counter()
         oracle.forward(feat, shape, start, loc, w, nthreads=nthreads)
         oracle.backward(feat, shape, start, loc, w, go)
-        dt = time.perf_counter() - t0
+        return time.perf_counter() - t0
+
+    # a call costs a fixed part (the backward allocates and clears the FP64 feature gradient) plus a part per
+    # anchor: the fixed part is timed on one anchor, and each step's anchor sample is sized so that the whole run
+    # stays within about three minutes (at least 8 anchors a step)
+    fixed = min(step([0]), step([1 % A]))
+    budget_s = 180.0
+    per_anchor_s = 0.02
+    na = int(max(8, min(A, (budget_s / max(1, args.steps + args.warmup) - fixed) / per_anchor_s)))
+    na = min(na, A)
+    times, raw = [], []
+    for it in range(args.warmup + args.steps):
+        a0 = (it * na) % A
+        dt = step([(a0 + j) % A for j in range(na)])
         if it >= args.warmup:
-            times.append(dt * A / na)
+            times.append(dt if na == A else fixed + (dt - fixed) * (A - 1) / (na - 1))
             raw.append(dt)
     v = statistics.mean(times) * 1e6
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
@@ -643,10 +662,11 @@ def run_reference(args, rank, world):
             "config": {"workload": wl_desc, "parallelism": "host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                              "sample": f"{na} anchors of {A} per step (forward on {nthreads} threads, backward "
-                                       f"single-threaded), scaled to a frame by {A}/{na}"},
+                                       f"single-threaded); a frame = the per-call cost ({fixed:.2f} s, timed on one "
+                                       f"anchor) + the sample's per-anchor part scaled to {A} anchors"},
             # value and ms_per_step are a frame's time extrapolated from the anchor sample, not the wall time of
             # a step; measured_ms_per_step is the sample's own time
-            "extrapolated": na < A, "frame_scale": A / na,
+            "extrapolated": na < A, "frame_scale": A / na, "per_call_s": fixed,
             "measured_ms_per_step": statistics.mean(raw) * 1e3,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
