@@ -131,9 +131,10 @@ def split_step(sub, grad_out, forward, backward, group=None):
 
 def backward_launches(det, zeroed=False):
     """Kernels msda_backward enqueues on the benchmark frame: atomic: the scatter kernel (and a memset unless
-    the forward cleared grad_feat); deterministic: dloc/dw, the cell-binned plan, binning and reduce, and the ten
-    corner-slot launches that find the cell-binned flag set and return at once."""
-    return 14 if det else (1 if zeroed else 2)
+    the forward cleared grad_feat); deterministic: the cell-binned plan, location transpose, binning and reduce,
+    dloc/dw, and the one-thread launcher that issues the corner-slot form from the device only when the
+    cell-binned plan has cleared its flag (it does not on this frame)."""
+    return 6 if det else (1 if zeroed else 2)
 
 
 def peaks():

@@ -500,17 +500,61 @@ __global__ void __launch_bounds__(256) det_reduce_kernel(const RedArgs a) {
     }
 }
 
-using RedKernel = void (*)(const RedArgs);
+// Launch parameters of the corner-slot form, computed on the host.  enqueue_corner_slot issues its kernels in
+// order on `stream`: from the host (the cell-binned path does not apply), or from det_fallback_kernel on the
+// device as tail launches (they run one after the other, after the launching grid, before the stream's next
+// work), only when the cell-binned plan has cleared its flag; so a backward that the cell-binned path
+// completes costs one single-thread launch here instead of ten empty grids.
+struct SlotLaunch {
+    KeyArgs ka;
+    RedArgs ra;
+    uint32_t *vals, *e_om, *e_pt, *e_ba, *cnt, *rowptr, *tsum;
+    long long nrows, nkb, kgrid, zb, ab, sb, pb, rgrid, ntiles, n;
+    unsigned segblocks;
+    size_t prep_smem;
+    int red_w;        // weights of the reduce: 0 FP32, 1 BF16, 2 FP16
+    int red_cpl;      // channels per lane of the reduce (4, 8, 16, 32)
+    const int* flag;  // the cell-binned plan's flag (device launcher only)
+    const int* gate;  // the flag for the kernels to read themselves (launches recorded in a graph capture), or NULL
+};
 
 template <typename WT>
-static RedKernel red_pick(int cpl) {
-    switch (cpl) {
-        case 4: return det_reduce_kernel<WT, 4>;
-        case 8: return det_reduce_kernel<WT, 8>;
-        case 16: return det_reduce_kernel<WT, 16>;
-        case 32: return det_reduce_kernel<WT, 32>;
+__host__ __device__ void enqueue_reduce(const SlotLaunch& s, cudaStream_t stream) {
+    const unsigned g = (unsigned)s.rgrid;
+    switch (s.red_cpl) {
+        case 4: det_reduce_kernel<WT, 4><<<g, 256, 0, stream>>>(s.ra); break;
+        case 8: det_reduce_kernel<WT, 8><<<g, 256, 0, stream>>>(s.ra); break;
+        case 16: det_reduce_kernel<WT, 16><<<g, 256, 0, stream>>>(s.ra); break;
+        default: det_reduce_kernel<WT, 32><<<g, 256, 0, stream>>>(s.ra); break;
     }
-    return nullptr;
+}
+
+__host__ __device__ void enqueue_corner_slot(const SlotLaunch& s, cudaStream_t stream) {
+    // per-row counts of the in-bound corners, row offsets (three-step scan), then the slot ids in place
+    det_zero_kernel<<<(unsigned)s.zb, 256, 0, stream>>>(s.cnt, s.nrows + 1, s.gate);
+    if (s.nkb > 0) det_rows_kernel<false><<<(unsigned)s.kgrid, 256, 0, stream>>>(s.ka);
+    row_scan_tile_kernel<<<(unsigned)s.ntiles, 1024, 0, stream>>>(s.cnt, s.nrows, s.rowptr, s.tsum, s.gate);
+    row_scan_totals_kernel<<<1, 1024, 0, stream>>>(s.tsum, (int)s.ntiles, s.rowptr + s.nrows, s.gate);
+    row_scan_add_kernel<<<(unsigned)s.ab, 256, 0, stream>>>(s.rowptr, s.tsum, s.nrows, s.gate);
+    if (s.nkb > 0) {
+        det_rows_kernel<true><<<(unsigned)s.kgrid, 256, 0, stream>>>(s.ka);
+        // the per-row counts are all zero again after the fill: their array takes the list of long rows
+        det_segsort_short_kernel<<<(unsigned)s.sb, 256, 0, stream>>>(s.rowptr, s.nrows, s.vals, s.cnt, s.cnt + s.nrows,
+                                                                      s.gate);
+        det_segsort_long_kernel<<<s.segblocks, kSegWarps * 32, 0, stream>>>(s.rowptr, s.cnt, s.cnt + s.nrows, s.vals,
+                                                                              s.e_om, s.gate);
+    }
+    if (s.n > 0)
+        det_prep_kernel<<<(unsigned)s.pb, 256, s.prep_smem, stream>>>(s.ra, (size_t)s.n, reinterpret_cast<float*>(s.e_om),
+                                                                       s.e_pt, s.e_ba);
+    if (s.red_w == 0) enqueue_reduce<float>(s, stream);
+    else if (s.red_w == 1) enqueue_reduce<__nv_bfloat16>(s, stream);
+    else enqueue_reduce<__half>(s, stream);
+}
+
+__global__ void det_fallback_kernel(const SlotLaunch s) {
+    if (*reinterpret_cast<const volatile int*>(s.flag)) return;  // the cell-binned path computed the gradient
+    enqueue_corner_slot(s, cudaStreamTailLaunch);
 }
 
 msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
@@ -542,9 +586,8 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
         }
     }
     const int cpl = p.C / red_rt;
-    RedKernel red = (p.w_t == MSDA_F32) ? red_pick<float>(cpl)
-                  : (p.w_t == MSDA_BF16) ? red_pick<__nv_bfloat16>(cpl) : red_pick<__half>(cpl);
-    if (!red) return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: no reduce kernel for %d channels per lane", cpl);
+    if (cpl != 4 && cpl != 8 && cpl != 16 && cpl != 32)
+        return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: no reduce kernel for %d channels per lane", cpl);
 
     // dloc and dw (no feature scatter)
     st = launch_backward_locw(p, grad_out, grad_loc, grad_w, warps, stream);
@@ -560,69 +603,68 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     }
 
     unsigned char* base = reinterpret_cast<unsigned char*>(ws);
-    uint32_t* vals = reinterpret_cast<uint32_t*>(base + L.vals);
-    uint32_t* e_om = reinterpret_cast<uint32_t*>(base + L.e_om);
-    uint32_t* e_pt = reinterpret_cast<uint32_t*>(base + L.e_pt);
-    uint32_t* e_ba = reinterpret_cast<uint32_t*>(base + L.e_ba);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(base + L.cnt);
-    uint32_t* rowptr = reinterpret_cast<uint32_t*>(base + L.rowptr);
-    uint32_t* tsum = reinterpret_cast<uint32_t*>(base + L.tsum);
-    KeyArgs ka;
+    SlotLaunch sl;
+    sl.vals = reinterpret_cast<uint32_t*>(base + L.vals);
+    sl.e_om = reinterpret_cast<uint32_t*>(base + L.e_om);
+    sl.e_pt = reinterpret_cast<uint32_t*>(base + L.e_pt);
+    sl.e_ba = reinterpret_cast<uint32_t*>(base + L.e_ba);
+    sl.cnt = reinterpret_cast<uint32_t*>(base + L.cnt);
+    sl.rowptr = reinterpret_cast<uint32_t*>(base + L.rowptr);
+    sl.tsum = reinterpret_cast<uint32_t*>(base + L.tsum);
+    sl.nrows = nrows;
+    KeyArgs& ka = sl.ka;
     ka.shape = p.shape; ka.start = p.start; ka.loc = p.loc; ka.npts = npts; ka.sum_hw = p.sum_hw; ka.A = p.A;
-    ka.P = p.P; ka.Ncam = p.Ncam; ka.Nscale = p.Nscale; ka.sbits = sbits; ka.cnt = cnt; ka.rowptr = rowptr;
-    ka.vals = vals; ka.status = dev.status; ka.gate = gate;
-    const long long nkb = (npts + kKeyBlock - 1) / kKeyBlock;
-    ka.nblk = nkb;
-    const long long kgrid = nkb < (long long)dev.sm_count * 8 ? nkb : (long long)dev.sm_count * 8;
-    // per-row counts of the in-bound corners, row offsets (three-step scan), then the slot ids in place
-    {
-        long long zb = (nrows + 1 + 255) / 256;
-        if (zb > (long long)dev.sm_count * 8) zb = (long long)dev.sm_count * 8;
-        det_zero_kernel<<<(unsigned)zb, 256, 0, stream>>>(cnt, nrows + 1, gate);
-    }
-    if (nkb > 0) det_rows_kernel<false><<<(unsigned)kgrid, 256, 0, stream>>>(ka);
-    row_scan_tile_kernel<<<(unsigned)L.ntiles, 1024, 0, stream>>>(cnt, nrows, rowptr, tsum, gate);
-    row_scan_totals_kernel<<<1, 1024, 0, stream>>>(tsum, L.ntiles, rowptr + nrows, gate);
-    {
-        long long ab = (nrows + 255) / 256;
-        if (ab > (long long)dev.sm_count * 8) ab = (long long)dev.sm_count * 8;
-        row_scan_add_kernel<<<(unsigned)ab, 256, 0, stream>>>(rowptr, tsum, nrows, gate);
-    }
-    if ((st = check_launch("msda_backward row offsets")) != MSDA_OK) return st;
-    if (nkb > 0) {
-        det_rows_kernel<true><<<(unsigned)kgrid, 256, 0, stream>>>(ka);
-        // the per-row counts are all zero again after the fill: their array takes the list of long rows
-        long long sb = (nrows + 255) / 256;
-        if (sb > (long long)dev.sm_count * 8) sb = (long long)dev.sm_count * 8;
-        det_segsort_short_kernel<<<(unsigned)sb, 256, 0, stream>>>(rowptr, nrows, vals, cnt, cnt + nrows, gate);
-        det_segsort_long_kernel<<<(unsigned)dev.sm_count * 8, kSegWarps * 32, 0, stream>>>(rowptr, cnt, cnt + nrows,
-                                                                                          vals, e_om, gate);
-        if ((st = check_launch("msda_backward row groups")) != MSDA_OK) return st;
-    }
-    RedArgs ra;
+    ka.P = p.P; ka.Ncam = p.Ncam; ka.Nscale = p.Nscale; ka.sbits = sbits; ka.cnt = sl.cnt; ka.rowptr = sl.rowptr;
+    ka.vals = sl.vals; ka.status = dev.status; ka.gate = nullptr;
+    const long long cap8 = (long long)dev.sm_count * 8;  // grid-stride kernels: one wave of 8 blocks per SM
+    sl.nkb = (npts + kKeyBlock - 1) / kKeyBlock;
+    ka.nblk = sl.nkb;
+    sl.kgrid = sl.nkb < cap8 ? sl.nkb : cap8;
+    sl.zb = (nrows + 1 + 255) / 256;
+    if (sl.zb > cap8) sl.zb = cap8;
+    sl.ab = (nrows + 255) / 256;
+    if (sl.ab > cap8) sl.ab = cap8;
+    sl.sb = sl.ab;
+    sl.segblocks = (long long)dev.sm_count * 8;
+    sl.ntiles = L.ntiles;
+    RedArgs& ra = sl.ra;
     ra.shape = p.shape; ra.start = p.start; ra.loc = p.loc; ra.w = p.w; ra.go = grad_out;
-    ra.vals = vals; ra.rowptr = rowptr; ra.gfeat = grad_feat; ra.nrows = nrows;
-    ra.e_om = reinterpret_cast<const float*>(e_om);
-    ra.e_pt = e_pt;
-    ra.e_ba = e_ba;
+    ra.vals = sl.vals; ra.rowptr = sl.rowptr; ra.gfeat = grad_feat; ra.nrows = nrows;
+    ra.e_om = reinterpret_cast<const float*>(sl.e_om);
+    ra.e_pt = sl.e_pt;
+    ra.e_ba = sl.e_ba;
     ra.wide = (((uintptr_t)grad_out % 32) == 0 && ((size_t)p.C * 4) % 32 == 0) ? 1 : 0;
     ra.sum_hw = p.sum_hw; ra.C = p.C; ra.Ncam = p.Ncam; ra.Nscale = p.Nscale; ra.A = p.A; ra.P = p.P;
-    ra.G = p.G; ra.Cg = p.Cg; ra.rt = red_rt; ra.sbits = sbits; ra.status = dev.status; ra.gate = gate;
+    ra.G = p.G; ra.Cg = p.Cg; ra.rt = red_rt; ra.sbits = sbits; ra.status = dev.status; ra.gate = nullptr;
     ra.ncam = make_fastdiv((uint32_t)(p.Ncam > 0 ? p.Ncam : 1));
     ra.pncam = make_fastdiv((uint32_t)((long long)p.P * p.Ncam > 0 ? (long long)p.P * p.Ncam : 1));
-    const size_t smem = sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale;
-    if (L.n > 0) {
-        if ((st = ensure_smem((const void*)det_prep_kernel, smem, dev)) != MSDA_OK) return st;
-        long long pb = ((long long)L.n + 255) / 256;
-        if (pb > (long long)dev.sm_count * 8) pb = (long long)dev.sm_count * 8;
-        det_prep_kernel<<<(unsigned)pb, 256, smem, stream>>>(ra, L.n, reinterpret_cast<float*>(e_om), e_pt, e_ba);
-        if ((st = check_launch("msda_backward prep")) != MSDA_OK) return st;
-    }
+    sl.n = (long long)L.n;
+    sl.prep_smem = sizeof(MapInfo) * (size_t)p.Ncam * p.Nscale;
+    if (sl.n > 0 && (st = ensure_smem((const void*)det_prep_kernel, sl.prep_smem, dev)) != MSDA_OK) return st;
+    sl.pb = (sl.n + 255) / 256;
+    if (sl.pb > cap8) sl.pb = cap8;
     const int nteams = 8 * (32 / red_rt);
     ra.nrb = (nrows + nteams - 1) / nteams;
-    const long long rgrid = ra.nrb < (long long)dev.sm_count * 8 ? ra.nrb : (long long)dev.sm_count * 8;
-    red<<<(unsigned)rgrid, 256, 0, stream>>>(ra);
-    return check_launch("msda_backward reduce");
+    sl.rgrid = ra.nrb < cap8 ? ra.nrb : cap8;
+    sl.red_w = p.w_t == MSDA_F32 ? 0 : p.w_t == MSDA_BF16 ? 1 : 2;
+    sl.red_cpl = cpl;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (gate && cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return check_launch("msda_backward capture query");
+    sl.flag = gate;
+    sl.gate = nullptr;
+    if (gate && cap == cudaStreamCaptureStatusNone) {
+        // the cell-binned path is in the stream: one thread checks its flag and issues the corner-slot kernels
+        // as tail launches only when the flag is clear
+        det_fallback_kernel<<<1, 1, 0, stream>>>(sl);
+    } else {
+        // no cell-binned path, or a graph capture (its replays do not run the tail launches): the kernels are
+        // enqueued here, each returning at once when the flag is set
+        sl.gate = gate;
+        sl.ka.gate = gate;
+        sl.ra.gate = gate;
+        enqueue_corner_slot(sl, stream);
+    }
+    return check_launch("msda_backward corner-slot form");
 }
 
 }  // namespace msda

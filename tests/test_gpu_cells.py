@@ -221,3 +221,49 @@ def test_random_problems(seed):
                              feat_dtype=fdt, w_dtype=wdt)
     check(pr, f"random {seed}: {ncam}x{nscale} maps, C={C} G={G} {fdt}/{wdt}, loc ({lo:.2f}, {hi:.2f})",
           expect_cells=False)
+
+
+def _overlapping(pr):
+    start = pr.scale_start_index.clone()
+    start[1, 0] = 2  # camera 1 scale 0 overlaps camera 0: the plan clears its flag
+    return inputs.Problem(pr.feat, pr.spatial_shape, start, pr.sampling_location, pr.weights, pr.grad_out)
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_deterministic_backward_replayed_from_a_cuda_graph(overlap):
+    """The deterministic backward captured in a CUDA graph and replayed gives the eager gradients bitwise: on the
+    cell-binned path, and, with overlapping maps, on the corner-slot form that the path's launcher issues from the
+    device after reading the plan's flag."""
+    gen = torch.Generator().manual_seed(7)
+    pr = inputs.make_problem(gen, B=1, cam_maps=[[(6, 5), (3, 2)], [(4, 4), (2, 2)]], C=32, G=4, A=9, P=3)
+    if overlap:
+        pr = _overlapping(pr)
+    d = pr.to("cuda")
+    T = (d.feat, d.spatial_shape, d.scale_start_index, d.sampling_location, d.weights)
+    B, sum_hw, C = d.feat.shape
+    _, A, P, K, _ = d.sampling_location.shape
+    S, G = d.weights.shape[4], d.weights.shape[5]
+    ws = torch.empty(msda.backward_workspace_size(B, sum_hw, C, K, S, A, P, G, True), dtype=torch.uint8,
+                     device="cuda")
+    grads = (torch.empty(B, sum_hw, C, device="cuda"), torch.empty(B, A, P, K, 2, device="cuda"),
+             torch.empty(B, A, P, K, S, G, device="cuda"))
+    msda.backward(*T, d.grad_out, deterministic=True, workspace=ws, grads=grads)  # eager, outside capture
+    torch.cuda.synchronize()
+    ref = [x.clone() for x in grads]
+    assert int(ws[:4].view(torch.int32).item()) == (0 if overlap else 1)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            msda.backward(*T, d.grad_out, deterministic=True, workspace=ws, grads=grads)
+    for _ in range(3):
+        for x in grads:
+            x.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for x, r in zip(grads, ref):
+            assert torch.equal(x, r)
+    assert msda.device_status() == 0
+    rf = oracle_backward(pr)
+    for x, r in zip(grads, rf):
+        assert relerr(x.cpu().double().numpy(), r) <= TOL_FP32
