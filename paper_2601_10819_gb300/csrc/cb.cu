@@ -707,6 +707,7 @@ __device__ __noinline__ void cb_sweep_in_place(const CbArgs& a, const float4* __
         if (r0 >= r1) continue;
         float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), nxt = cur;
         long long ci = pm + (long long)r0 * W1 + j;  // left cell of cell row r0 - 1
+#pragma unroll 2
         for (int cy = r0 - 1; cy < r1; ++cy) {
             const uint32_t q0 = Cp[ci], q1 = Cp[ci + 1], q2 = Cp[ci + 2];
             if (cy < r0) {
@@ -858,6 +859,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) cb_reduce_kernel(const CbArgs a
                             float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), nxt = cur;
                             // left cell of cell row r0 - 1 (cell row index r0), as a slot of the staged pointers
                             int ci = (int)(pm - (long long)bd.ca0) + r0 * W1 + j;
+#pragma unroll 2
                             for (int cy = r0 - 1; cy < r1; ++cy) {
                                 const uint32_t q0 = Cp[ci], q1 = Cp[ci + 1], q2 = Cp[ci + 2];
                                 if (cy < r0) {
