@@ -47,7 +47,7 @@ struct CbMap {
 };
 
 struct CbHeader {
-    int ok;           // 1: this path runs and the corner-slot kernels return at once
+    int ok;           // 1: this path runs and the corner-slot form is not issued
     int ngaps;        // row ranges of a batch element that no valid map covers
     int pad[62];
 };

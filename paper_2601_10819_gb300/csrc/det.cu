@@ -69,7 +69,8 @@ size_t backward_det_workspace(const Problem& p) {
     return slots > cells ? slots : cells;
 }
 
-// True when the cell-binned path ran and set its flag: the corner-slot kernels have nothing to do.
+// True when the cell-binned path ran and set its flag: the corner-slot kernels have nothing to do (they read the
+// flag themselves only when they were recorded in a graph capture; otherwise they are launched only if needed).
 __device__ __forceinline__ bool gated(const int* gate) { return gate && *reinterpret_cast<const volatile int*>(gate); }
 
 __global__ void __launch_bounds__(256) det_zero_kernel(uint32_t* __restrict__ p, long long n, const int* gate) {
@@ -594,8 +595,9 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     if (st != MSDA_OK) return st;
     if (nrows == 0) return MSDA_OK;
 
-    // The feature gradient: the cell-binned path when it applies (decided on the device for the maps; its
-    // flag then turns the corner-slot kernels below into empty launches), else the corner-slot path.
+    // The feature gradient: the cell-binned path when it applies (decided on the device for the maps), else the
+    // corner-slot path, which the launcher below issues from the device only when the cell-binned plan has
+    // cleared its flag.
     const int* gate = nullptr;
     if (allow_cells && cb_shape_ok(p) && cb_device_ok(p, dev)) {
         if ((st = launch_backward_cb(p, grad_out, grad_feat, ws, body, stream)) != MSDA_OK) return st;
