@@ -556,6 +556,8 @@ __host__ __device__ void enqueue_corner_slot(const SlotLaunch& s, cudaStream_t s
 __global__ void det_fallback_kernel(const SlotLaunch s) {
     if (*reinterpret_cast<const volatile int*>(s.flag)) return;  // the cell-binned path computed the gradient
     enqueue_corner_slot(s, cudaStreamTailLaunch);
+    // a launch the device runtime refused leaves the gradient unwritten: say so in the status word
+    if (cudaGetLastError() != cudaSuccess) raise_status(s.ka.status, MSDA_ERR_CUDA);
 }
 
 msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
