@@ -51,10 +51,16 @@
  *   msda_last_error() gives a message for the last failing call of the
  *   calling thread.
  * - Streams: `stream` is a cudaStream_t (NULL = legacy default stream); all
- *   work is enqueued on it.  The calls allocate nothing and do not
+ *   work is ordered on it.  The calls allocate nothing and do not
  *   synchronise, so they may be captured in a CUDA graph, except that the
  *   first call on a device looks up the device status word and reads
- *   device attributes, which should happen before any capture.
+ *   device attributes, which should happen before any capture.  The
+ *   deterministic msda_backward runs its cell-binned kernels on a second
+ *   stream of the library's (one per device, made by the first such call
+ *   outside a capture), forked from `stream` and joined back to it with
+ *   events inside the call, so everything enqueued on `stream` afterwards
+ *   sees the whole result and a capture of `stream` takes those kernels in
+ *   as a parallel branch.
  */
 #ifndef MSDA_GB300_H
 #define MSDA_GB300_H

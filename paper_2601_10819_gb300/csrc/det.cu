@@ -19,6 +19,8 @@
 // with shifts and two divisions by constants (multiply-high).  The reduce
 // kernel recomputes the corner weight omega from the location with the same
 // arithmetic as every other kernel, so keys and weights agree.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 #include "wsort.cuh"
@@ -560,6 +562,43 @@ __global__ void det_fallback_kernel(const SlotLaunch s) {
     if (cudaGetLastError() != cudaSuccess) raise_status(s.ka.status, MSDA_ERR_CUDA);
 }
 
+// A second stream per device for the cell-binned kernels, which read nothing the dloc/dw kernel writes: the
+// two chains run side by side (the binning kernel alone fills under two blocks per SM).  Events fork the side
+// stream from the caller's stream and join it back before anything that reads the flag or the gradient, so the
+// call stays ordered on the caller's stream, and a graph capture of that stream takes the side stream's kernels
+// in as a parallel branch.  The mutex is held from the fork to the join, so calls from several host threads do
+// not interleave their events.
+struct SideStream {
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+static std::mutex g_side_mu;
+static SideStream g_side[128];
+static signed char g_side_state[128];  // 0: not made yet, 1: made, -1: creation failed (no side stream)
+
+// The device's side stream, made on the first call outside a graph capture; nullptr while none exists.  The
+// caller holds g_side_mu.
+static SideStream* side_stream(int device, bool may_create) {
+    if (device < 0 || device >= 128) return nullptr;
+    if (g_side_state[device] == 0 && may_create) {
+        SideStream ss;
+        if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) == cudaSuccess) {
+            if (cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess) {
+                if (cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) == cudaSuccess) {
+                    g_side[device] = ss;
+                    g_side_state[device] = 1;
+                    return &g_side[device];
+                }
+                cudaEventDestroy(ss.fork);
+            }
+            cudaStreamDestroy(ss.s);
+        }
+        (void)cudaGetLastError();  // the call runs on the caller's stream alone; no error is left behind
+        g_side_state[device] = -1;
+    }
+    return g_side_state[device] == 1 ? &g_side[device] : nullptr;
+}
+
 msda_status launch_backward_det(const Problem& p, const float* grad_out, float* grad_feat,
                                 float* grad_loc, float* grad_w, void* ws, size_t ws_bytes,
                                 int warps, bool allow_cells, cudaStream_t stream) {
@@ -592,19 +631,38 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     if (cpl != 4 && cpl != 8 && cpl != 16 && cpl != 32)
         return fail(MSDA_ERR_UNSUPPORTED, "msda_backward: no reduce kernel for %d channels per lane", cpl);
 
-    // dloc and dw (no feature scatter)
-    st = launch_backward_locw(p, grad_out, grad_loc, grad_w, warps, stream);
-    if (st != MSDA_OK) return st;
-    if (nrows == 0) return MSDA_OK;
-
     // The feature gradient: the cell-binned path when it applies (decided on the device for the maps), else the
     // corner-slot path, which the launcher below issues from the device only when the cell-binned plan has
-    // cleared its flag.
+    // cleared its flag.  The cell-binned kernels go to the side stream, beside dloc and dw (no feature scatter)
+    // on the caller's stream.
+    const bool cells = nrows > 0 && allow_cells && cb_shape_ok(p) && cb_device_ok(p, dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cells && cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return check_launch("msda_backward capture query");
+    std::unique_lock<std::mutex> side_lock(g_side_mu, std::defer_lock);
+    SideStream* side = nullptr;
+    if (cells) {
+        side_lock.lock();
+        side = side_stream(dev.device, cap == cudaStreamCaptureStatusNone);
+        if (side && (cudaEventRecord(side->fork, stream) != cudaSuccess ||
+                     cudaStreamWaitEvent(side->s, side->fork, 0) != cudaSuccess))
+            return check_launch("msda_backward side-stream fork");
+    }
     const int* gate = nullptr;
-    if (allow_cells && cb_shape_ok(p) && cb_device_ok(p, dev)) {
-        if ((st = launch_backward_cb(p, grad_out, grad_feat, ws, body, stream)) != MSDA_OK) return st;
+    msda_status st_cells = MSDA_OK;
+    if (cells) {
+        st_cells = launch_backward_cb(p, grad_out, grad_feat, ws, body, side ? side->s : stream);
         gate = reinterpret_cast<const int*>(ws);
     }
+    st = launch_backward_locw(p, grad_out, grad_loc, grad_w, warps, stream);
+    if (side) {
+        // joined whatever the launches above returned, so no capture is left with an unjoined branch
+        if (cudaEventRecord(side->join, side->s) != cudaSuccess || cudaStreamWaitEvent(stream, side->join, 0) != cudaSuccess)
+            return check_launch("msda_backward side-stream join");
+        side_lock.unlock();
+    }
+    if (st != MSDA_OK) return st;
+    if (st_cells != MSDA_OK) return st_cells;
+    if (nrows == 0) return MSDA_OK;
 
     unsigned char* base = reinterpret_cast<unsigned char*>(ws);
     SlotLaunch sl;
@@ -652,8 +710,6 @@ msda_status launch_backward_det(const Problem& p, const float* grad_out, float* 
     sl.rgrid = ra.nrb < cap8 ? ra.nrb : cap8;
     sl.red_w = p.w_t == MSDA_F32 ? 0 : p.w_t == MSDA_BF16 ? 1 : 2;
     sl.red_cpl = cpl;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (gate && cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return check_launch("msda_backward capture query");
     sl.flag = gate;
     sl.gate = nullptr;
     if (gate && cap == cudaStreamCaptureStatusNone) {
